@@ -1,0 +1,596 @@
+"""Pins of the FP64 oracle against closed forms, invariants and limits.
+
+Each test fixes a result the paper's method must reach by mathematics alone
+(straight rays in uniform media, exact RK4 on parabolic rays, Bouguer's
+invariant and the deflection integral in spherical symmetry, I*S = const with
+emission off (Eq. 1), T_b -> T_e for an optically thick isothermal medium,
+the small-step law of the step-wise magnification (Eqs. 5-11)), chosen so
+that a dropped term, a wrong sign or index, or a transposed operand anywhere
+in the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import corona_synth as cs
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+F100 = 100e6
+
+
+def frame(lon=0.0, lat=0.0):
+    o = np.array([math.cos(lat) * math.cos(lon), math.cos(lat) * math.sin(lon), math.sin(lat)])
+    eu = np.array([-math.sin(lon), math.cos(lon), 0.0])
+    ev = np.array([-math.sin(lat) * math.cos(lon), -math.sin(lat) * math.sin(lon), math.cos(lat)])
+    return o, eu, ev
+
+
+def pixel_uv(v, pix):
+    ix, iy = pix % v.nx, pix // v.nx
+    return (v.x0 + (ix + 0.5) * (v.x1 - v.x0) / v.nx, v.y0 + (iy + 0.5) * (v.y1 - v.y0) / v.ny)
+
+
+# ------------------------------------------------------------ uniform / vacuum
+
+def test_uniform_medium_straight_chords(orc):
+    """Uniform n_e inside the sphere: straight chords, M = 1, closed-form T_b."""
+    ne0, te0, rmin, rmax = 5e7, 1.5e6, 1.0, 4.0
+    F = orc.analytic_field(orc.UNIFORM, rmin, rmax, ne0=ne0, te0=te0)
+    v = cs.View(0.3, 0.2, 9, 7, -3.6, 3.6, -3.0, 3.0)
+    opts = orc.default_options(tbc_mode=1, tbc_K=7.5e5)
+    res = orc.trace(F, v, [F100], opts)
+    n = math.sqrt(1.0 - orc.c_pe() * ne0 / F100 ** 2)
+    kap = orc.kappa_vac(ne0, te0, F100) * orc.r_sun_cm()  # per R_sun
+    o, eu, ev = frame(0.3, 0.2)
+    for pix in range(v.nx * v.ny):
+        u, w = pixel_uv(v, pix)
+        b2 = u * u + w * w
+        if b2 >= rmax ** 2:
+            assert res["status"][0, pix] == 5 and res["tb"][0, pix] == 0.0
+            continue
+        p = u * eu + w * ev
+        zin = math.sqrt(rmax ** 2 - b2)
+        if b2 < rmin ** 2:
+            L = zin - math.sqrt(rmin ** 2 - b2)
+            end = p + math.sqrt(rmin ** 2 - b2) * o
+            tb = te0 * -math.expm1(-kap * L / n) + 7.5e5 * math.exp(-kap * L / n)
+            status = 2
+        else:
+            L = 2 * zin
+            end = p - zin * o
+            tb = te0 * -math.expm1(-kap * L / n)
+            status = 1
+        assert res["status"][0, pix] == status
+        # FP64 rounding of eps-sized differences of absolute positions leaves
+        # |ln M| ~ 1e-12 per step (the neighbours differ by eps = 1e-3)
+        assert abs(res["tb"][0, pix] - tb) <= 1e-9 * tb
+        assert abs(res["ln_s"][0, pix]) < 1e-9
+        np.testing.assert_allclose(res["exit"][0, pix], end, atol=1e-11)
+        # tau of the chord: kappa L / n (kappa = kappa_vac / n, ds = n dtau)
+        assert abs(res["tau"][0, pix] - kap * L / n) <= 1e-11 * kap * L / n
+
+
+def test_uniform_grid_equals_analytic(orc):
+    """A grid whose nodes all hold one value reproduces the analytic uniform medium."""
+    g = cs.newkirk_grid(12, 6, 10, 4.0)
+    g.ne[...] = 5e7
+    g.te[...] = 1.5e6
+    Fg = orc.grid_field(g)
+    Fa = orc.analytic_field(orc.UNIFORM, 1.0, 4.0, ne0=5e7, te0=1.5e6)
+    v = cs.View(1.1, -0.4, 6, 6, -3.2, 3.2, -3.2, 3.2)
+    for mode in (orc.STEPWISE, orc.TUBE):
+        o = orc.default_options(s_mode=mode)
+        a = orc.trace(Fa, v, [F100, 300e6], o)
+        b = orc.trace(Fg, v, [F100, 300e6], o)
+        np.testing.assert_allclose(b["tb"], a["tb"], rtol=1e-11)
+        np.testing.assert_allclose(b["exit"], a["exit"], atol=1e-10)
+        assert np.all(np.abs(b["ln_s"]) < 1e-9)
+
+
+def test_vacuum(orc):
+    """Vacuum: straight rays to the antipode, T_b = T_bc only on the disk."""
+    F = orc.analytic_field(orc.VACUUM, 1.0, 4.0, te0=1e6)
+    v = cs.View(0.0, 0.0, 8, 8, -2.0, 2.0, -2.0, 2.0)
+    res = orc.trace(F, v, [F100], orc.default_options(tbc_mode=1, tbc_K=4321.0))
+    o, eu, ev = frame()
+    for pix in range(64):
+        u, w = pixel_uv(v, pix)
+        b2 = u * u + w * w
+        if b2 < 1.0:
+            assert res["status"][0, pix] == 2 and res["tb"][0, pix] == pytest.approx(4321.0, rel=1e-14)
+        else:
+            assert res["status"][0, pix] == 1 and res["tb"][0, pix] == 0.0
+            end = u * eu + w * ev - math.sqrt(16 - b2) * o
+            np.testing.assert_allclose(res["exit"][0, pix], end, atol=1e-12)
+            steps = res["steps"][0, pix]
+            # |k| = 1 in vacuum, so the chord of 2 sqrt(R^2-b^2) takes ceil(L / h) steps
+            assert steps == math.ceil(2 * math.sqrt(16 - b2) / 2e-3)
+
+
+def test_miss_outside_sphere(orc):
+    g, _, _ = cs.tiny_workload()
+    F = orc.grid_field(g)
+    v = cs.View(0.0, 0.0, 4, 4, -6.0, 6.0, -6.0, 6.0)
+    res = orc.trace(F, v, [F100])
+    corners = [0, 3, 12, 15]
+    for p in corners:
+        assert res["status"][0, p] == 5 and res["tb"][0, p] == 0.0 and res["steps"][0, p] == 0
+
+
+# ------------------------------------------------------------------ linear slab
+
+def _slab(orc, ne0=2e6, c=-5.0, q=(0.0, 0.0, 1.0), rmin=0.05, rmax=4.0):
+    return orc.analytic_field(orc.SLAB, rmin, rmax, ne0=ne0, te0=1e6, q=q, c=c)
+
+
+def test_slab_parabola_exact(orc):
+    """Linear n^2 filling the sphere: constant force, RK4 reproduces the
+    parabola r = r0 + k0 tau + A tau^2 / 2 and H = 0 to rounding; the
+    step-wise magnification is exactly 1."""
+    ne0, f = 2e6, F100
+    F = _slab(orc, ne0)
+    v = cs.View(0.0, 0.0, 3, 3, -1.5, 1.5, -1.5, 1.5)
+    A = -orc.c_pe() / (2 * f * f) * ne0 * np.array([0.0, 0.0, 1.0])
+    o, eu, ev = frame()
+    for pix in range(9):
+        p = orc.trace_path(F, v, f, pix, orc.default_options())
+        r, k = p["r"], p["k"]
+        n_full = len(r) - 1  # last node is the clipped exit point
+        tau = np.arange(n_full)[:, None] * 2e-3
+        r0, k0 = r[0], k[0]
+        np.testing.assert_allclose(r[:n_full], r0 + k0 * tau + 0.5 * A * tau ** 2, atol=1e-12)
+        np.testing.assert_allclose(k[:n_full], k0 + A * tau, atol=1e-13)
+        n2 = 1 - orc.c_pe() * ne0 * (r[:n_full, 2] + 5.0) / f ** 2
+        assert np.max(np.abs(np.sum(k[:n_full] ** 2, 1) - n2)) < 1e-12
+        # M = 1 wherever every neighbour stage sees the same force: not on the
+        # first step (the neighbours straddle the vacuum outside the sphere)
+        # nor on the exit step
+        assert np.max(np.abs(np.diff(p["ln_s_path"][1: n_full - 1]))) < 1e-12
+
+
+def test_slab_tube_lockstep_closed_form(orc):
+    """Tube mode in a constant force: each neighbour is its own exact
+    parabola from its own entry point; S_{i+1} = |det[d1, d2, t^i]| with
+    central differences d_j and the central chord t^i."""
+    ne0, f, h, delta = 2e6, F100, 2e-3, 1e-3
+    F = _slab(orc, ne0, q=(0.3, 0.0, math.sqrt(1 - 0.09)))
+    q = np.array([0.3, 0.0, math.sqrt(1 - 0.09)])
+    A = -orc.c_pe() / (2 * f * f) * ne0 * q
+    v = cs.View(0.0, 0.0, 2, 2, -1.0, 1.0, -1.0, 1.0)
+    o, eu, ev = frame()
+    for n_nb in (2, 4, 8):
+        opts = orc.default_options(s_mode=orc.TUBE, n_nb=n_nb, delta=delta)
+        for pix in range(4):
+            p = orc.trace_path(F, v, f, pix, opts)
+            u, w = pixel_uv(v, pix)
+
+            def ray(du, dw, tau):
+                pp = (u + du) * eu + (w + dw) * ev
+                r0 = pp + math.sqrt(16 - (u + du) ** 2 - (w + dw) ** 2) * o
+                n0 = math.sqrt(1 - orc.c_pe() * ne0 * (q @ r0 + 5.0) / f ** 2)
+                return r0 + n0 * (-o) * tau + 0.5 * A * tau ** 2
+
+            m = len(p["r"]) - 2  # last full node
+            s = 1 / math.sqrt(2)
+            for i in (1, m // 3, m - 1):
+                t = ray(0, 0, i * h) - ray(0, 0, (i - 1) * h)
+                t /= np.linalg.norm(t)
+
+                def area(a, b):
+                    if n_nb == 2:
+                        d1 = ray(*a, i * h) - ray(0, 0, i * h)
+                        d2 = ray(*b, i * h) - ray(0, 0, i * h)
+                    else:
+                        d1 = 0.5 * (ray(*a, i * h) - ray(-a[0], -a[1], i * h))
+                        d2 = 0.5 * (ray(*b, i * h) - ray(-b[0], -b[1], i * h))
+                    return abs(np.cross(d1, d2) @ t)
+
+                S = area((delta, 0), (0, delta))
+                if n_nb == 8:
+                    S = 0.5 * (S + area((s * delta, s * delta), (-s * delta, s * delta)))
+                assert p["ln_s_path"][i] == pytest.approx(math.log(S / delta ** 2), abs=5e-9)
+
+
+def test_slab_tube_snell(orc):
+    """Tube mode across a slab surface: S/S0 = sqrt(n^2 - sin^2 th0)/(n cos th0)."""
+    f, ne0 = F100, 2e6
+    q = np.array([-math.sin(0.6), 0.0, math.cos(0.6)])
+    F = _slab(orc, ne0, c=-1.0, q=tuple(q))
+    v = cs.View(0.0, 0.0, 1, 1, -0.01, 0.01, -0.01, 0.01)
+    opts = orc.default_options(s_mode=orc.TUBE, delta=1e-2, dtau=5e-4, emission=0)
+    p = orc.trace_path(F, v, f, 0, opts)
+    depth = p["r"] @ q + 1.0
+    idx = np.where(depth > 0.5)[0][:50]
+    n2 = 1 - orc.c_pe() * ne0 * depth[idx] / f ** 2
+    cos0 = -q[0]
+    snell = np.sqrt(n2 - (1 - cos0 ** 2)) / (np.sqrt(n2) * cos0)
+    np.testing.assert_allclose(np.exp(p["ln_s_path"][idx]), snell, rtol=1e-4)
+
+
+# ---------------------------------------------------------- spherical symmetry
+
+def _newkirk_n(r, f):
+    import oracle
+    return np.sqrt(1 - oracle.c_pe() * 4.2e4 * 10 ** (4.32 / r) / f ** 2)
+
+
+@pytest.mark.parametrize("analytic", [True, False])
+def test_bouguer_invariant_and_hamiltonian(orc, analytic):
+    """|r x k| = n r sin psi is conserved in a spherically symmetric medium,
+    and H = (k^2 - n^2)/2 stays 0."""
+    if analytic:
+        F = orc.analytic_field(orc.NEWKIRK, 1.0, 4.0, te0=1e6)
+        tol_L, tol_H = 1e-8, 1e-8
+    else:
+        g, _, _ = cs.tiny_workload()
+        F = orc.grid_field(g)
+        # The trilinear interpolant's gradient jumps at every radial node
+        # (by ~dr / scale height of itself); RK4 commits an O(h^2 jump) error
+        # in H at each crossing, ~1e-6 per crossing here.  L stays exact
+        # because the force is exactly radial.
+        tol_L, tol_H = 1e-6, 2e-3
+    v = cs.View(0.0, 0.0, 16, 16, -2.5, 2.5, -2.5, 2.5)
+    for pix in (8 * 16 + 8, 8 * 16 + 12, 3 * 16 + 2, 15):
+        p = orc.trace_path(F, v, F100, pix)
+        r, k = p["r"][:-1], p["k"][:-1]
+        L = np.linalg.norm(np.cross(r, k), axis=1)
+        assert np.max(np.abs(L / L[0] - 1)) < tol_L
+        ne = p["ne"][:-1]
+        n2 = 1 - orc.c_pe() * ne / F100 ** 2
+        assert np.max(np.abs(np.sum(k * k, 1) - n2)) < tol_H
+
+
+def test_turning_radius_and_deflection(orc):
+    """Analytic Newkirk: min |r| = turning radius n(r_t) r_t = L, and the exit
+    point follows the deflection integral 2 int L dr / (r sqrt(n^2 r^2 - L^2))."""
+    f, R = F100, 4.0
+    F = orc.analytic_field(orc.NEWKIRK, 1.0, R, te0=1e6)
+    from scipy.optimize import brentq
+    for b in (0.3, 0.9, 1.6, 2.4):
+        v = cs.View(0.0, 0.0, 1, 1, b - 1e-9, b + 1e-9, -1e-9, 1e-9)
+        p = orc.trace_path(F, v, f, 0, orc.default_options(dtau=1e-3))
+        L = _newkirk_n(R, f) * b
+        r_crit = 4.32 / math.log10(f * f / (orc.c_pe() * 4.2e4))  # n = 0 there
+        rt = brentq(lambda r: _newkirk_n(r, f) * r - L, r_crit * (1 + 1e-12), R, xtol=1e-15)
+        rmin = np.min(np.linalg.norm(p["r"], axis=1))
+        assert abs(rmin - rt) < 2e-6
+
+        # substitute r = rt + s^2 to remove the endpoint singularity
+        def integrand(s):
+            r = rt + s * s
+            return 2 * s * L / (r * math.sqrt(max(_newkirk_n(r, f) ** 2 * r * r - L * L, 1e-300)))
+        dphi = 2 * integrate.quad(integrand, 0.0, math.sqrt(R - rt), epsabs=1e-13, epsrel=1e-13, limit=400)[0]
+        psi_in = math.atan2(b, math.sqrt(R * R - b * b))
+        ang = psi_in + dphi
+        exit_expect = R * np.array([math.cos(ang), math.sin(ang), 0.0])
+        assert p["status"] == 1
+        np.testing.assert_allclose(p["exit"], exit_expect, atol=1e-5)
+
+
+def test_critical_radius_100mhz(orc):
+    """The near-central ray turns at the 100 MHz critical layer, 1.245 R_sun."""
+    g, v, f = cs.tiny_workload()
+    F = orc.grid_field(g)
+    p = orc.trace_path(F, v, 100e6, 32 * 64 + 32)
+    assert abs(np.min(np.linalg.norm(p["r"], axis=1)) - 1.245) < 2e-3
+
+
+def test_longitude_and_image_symmetry(orc):
+    """Spherically symmetric media: the map does not depend on the observer
+    longitude, and is symmetric under image transposition and flips.
+
+    Exact with the magnification off.  The step-wise tube estimate depends on
+    the transverse basis only at O(eps^2) in a smooth field (central
+    differences) but at O(1) per step where a neighbour pair straddles one
+    of the trilinear interpolant's radial kinks; the basis axis rule (y
+    instead of z when |t_z| > 0.9) is not invariant under transposition, so
+    on the grid the symmetry holds only to the kink level."""
+    g, v, f = cs.tiny_workload()
+    Fg = orc.grid_field(g)
+    Fa = orc.analytic_field(orc.NEWKIRK, 1.0, 4.0, te0=1e6)
+    v = cs.View(0.0, 0.0, 12, 12, -2.5, 2.5, -2.5, 2.5)
+    v2 = cs.View(1.234, 0.0, 12, 12, -2.5, 2.5, -2.5, 2.5)
+    for F, mode, tol in ((Fg, orc.MAG_OFF, 1e-10), (Fa, orc.STEPWISE, 1e-8), (Fg, orc.STEPWISE, 1e-3)):
+        o = orc.default_options(s_mode=mode)
+        a = orc.trace(F, v, f, o)["tb"].reshape(12, 12)
+        b = orc.trace(F, v2, f, o)["tb"].reshape(12, 12)
+        np.testing.assert_allclose(b, a, rtol=tol)
+        np.testing.assert_allclose(a, a.T, rtol=tol)
+        np.testing.assert_allclose(a, a[::-1, :], rtol=tol)
+        np.testing.assert_allclose(a, a[:, ::-1], rtol=tol)
+
+
+def test_observer_longitude_matches_rolled_grid(orc):
+    """Rotating the observer by k phi-cells equals rolling the grid by -k cells."""
+    rng = np.random.default_rng(5)
+    g = cs.newkirk_grid(16, 12, 24, 4.0)
+    mod = 1 + 0.3 * rng.random(g.ne.shape)
+    g.ne = g.ne * mod
+    g.te = g.te * (1 + 0.5 * rng.random(g.ne.shape))
+    kshift = 5
+    lon = kshift * 2 * math.pi / 24
+    v = cs.View(lon, 0.0, 8, 8, -2.5, 2.5, -2.5, 2.5)
+    g2 = cs.Grid(g.r, g.theta, g.phi, np.roll(g.ne, -kshift, axis=2), np.roll(g.te, -kshift, axis=2))
+    # exact with the magnification off; the step-wise basis axis rule is not
+    # rotation invariant (see test_longitude_and_image_symmetry)
+    for mode, tol in ((orc.MAG_OFF, 1e-10), (orc.STEPWISE, 1e-4)):
+        o = orc.default_options(s_mode=mode)
+        a = orc.trace(orc.grid_field(g), v, [80e6, 300e6], o)
+        b = orc.trace(orc.grid_field(g2), cs.View(0.0, 0.0, 8, 8, -2.5, 2.5, -2.5, 2.5), [80e6, 300e6], o)
+        np.testing.assert_allclose(a["tb"], b["tb"], rtol=tol)
+        np.testing.assert_allclose(a["exit"], b["exit"].reshape(a["exit"].shape) @ np.array(
+            [[math.cos(lon), math.sin(lon), 0], [-math.sin(lon), math.cos(lon), 0], [0, 0, 1]]), atol=1e-9)
+
+
+# -------------------------------------------------------------- transfer pins
+
+def test_IS_conserved_without_emission(orc):
+    """Eq. 1: with j = kappa = 0 the transfer gives T_b = T_bc S_N / S_0."""
+    g, v, _ = cs.tiny_workload()
+    F = orc.grid_field(g)
+    v = cs.View(0.0, 0.0, 10, 10, -1.2, 1.2, -1.2, 1.2)
+    for mode in (orc.STEPWISE, orc.TUBE):
+        res = orc.trace(F, v, [400e6], orc.default_options(emission=0, tbc_mode=1, tbc_K=1e4, s_mode=mode))
+        hit = res["status"] == 2
+        assert hit.sum() > 20
+        np.testing.assert_allclose(res["tb"][hit], 1e4 * np.exp(res["ln_s"][hit]), rtol=1e-12)
+        assert np.any(np.abs(res["ln_s"][hit]) > 1e-4)  # the tube does change
+        assert np.all(res["tb"][~hit] == 0.0)
+
+
+def test_optically_thick_isothermal(orc):
+    """Isothermal medium, magnification off: T_b = T_e (1 - e^-tau) + T_bc e^-tau
+    exactly, and optically thick rays reach T_e.  With the magnification on,
+    T_b = T_e <S/S0> over the last few optical depths (I S = const along the
+    tube), so |T_b/T_e - 1| stays within a few times max |S/S0 - 1|."""
+    g, v, f = cs.tiny_workload()
+    te = 3e5
+    g.te[...] = te
+    F = orc.grid_field(g)
+    v = cs.View(0.0, 0.0, 8, 8, -1.0, 1.0, -1.0, 1.0)
+    r = orc.trace(F, v, [60e6, 100e6, 200e6], orc.default_options(s_mode=orc.MAG_OFF))
+    tbc = np.where(r["status"] == 2, te, 0.0)
+    expect = te * -np.expm1(-r["tau"]) + tbc * np.exp(-r["tau"])
+    np.testing.assert_allclose(r["tb"], expect, rtol=1e-12)
+    thick = r["tau"] > 36
+    assert thick.sum() > 10
+    np.testing.assert_allclose(r["tb"][thick], te, rtol=1e-14)
+    r2 = orc.trace(F, v, [60e6, 100e6], orc.default_options())
+    thick = r2["tau"] > 36
+    assert thick.sum() > 10
+    dev = np.abs(r2["tb"][thick] / te - 1)
+    bound = 3 * np.maximum(np.abs(np.expm1(r2["ln_s"][thick])), 1e-4)
+    assert np.all(dev <= bound)
+
+
+def test_tau_stop_and_step_limit(orc):
+    g, v, f = cs.tiny_workload()
+    F = orc.grid_field(g)
+    v = cs.View(0.0, 0.0, 4, 4, -0.5, 0.5, -0.5, 0.5)
+    r = orc.trace(F, v, [100e6], orc.default_options(tau_stop=5.0, s_mode=orc.MAG_OFF))
+    assert np.all(r["status"] == 3)
+    assert np.all((r["tau"] >= 5.0) & (r["tau"] < 5.5))
+    np.testing.assert_allclose(r["tb"], 1e6 * -np.expm1(-r["tau"]), rtol=1e-12)
+    r = orc.trace(F, v, [100e6], orc.default_options(max_steps=10))
+    assert np.all(r["status"] == 4) and np.all(r["steps"] == 10)
+
+
+def test_kappa_properties(orc):
+    """kappa_vac scales as n_e^2 and its two Gaunt branches meet at 2e5 K
+    (within 1.5%: the jump is 6.3 - ln(2e5)/2 = 0.2 in G), which fixes the two additive constants relative to each other."""
+    k1 = orc.kappa_vac(1e8, 1e6, 1e8)
+    assert orc.kappa_vac(2e8, 1e6, 1e8) == pytest.approx(4 * k1, rel=1e-14)
+    lo = orc.kappa_vac(1e8, 2e5 * (1 - 1e-12), 1e8)
+    hi = orc.kappa_vac(1e8, 2e5 * (1 + 1e-12), 1e8)
+    assert abs(hi / lo - 1) < 0.015
+    assert orc.kappa_vac(0.0, 1e6, 1e8) == 0.0
+    # Rayleigh-Jeans free-free with a Gaunt factor ~ 10 gives the same order
+    assert 0.3 < k1 / (0.018 * 1e6 ** -1.5 * 1e16 * 1e-16 * 10) < 3
+
+
+# ------------------------------------------------------------ integrator pins
+
+def test_rk4_fourth_order(orc):
+    """Global error of RK4 drops by 2^4 when the step halves."""
+    F = orc.analytic_field(orc.NEWKIRK, 1.0, 10.0, te0=1e6)
+    f = 80e6
+    r0 = np.array([2.0, 0.4, 0.1])
+    n0 = _newkirk_n(np.linalg.norm(r0), f)
+    k0 = n0 * np.array([-0.8, 0.6, 0.0])
+
+    def run(h, T=0.64):
+        r, k = r0.copy(), k0.copy()
+        for _ in range(int(round(T / h))):
+            r, k = orc.rk4_step(F, f, h, r, k)
+        return r
+
+    ref = run(0.64 / 4096)
+    e = [np.linalg.norm(run(h) - ref) for h in (0.04, 0.02, 0.01)]
+    assert 13 < e[0] / e[1] < 19 and 13 < e[1] / e[2] < 19
+
+
+@pytest.mark.parametrize("n_nb", [2, 4, 8])
+def test_stepwise_small_step_law(orc, n_nb):
+    """(M - 1)/h^2 -> tr_perp(grad grad n^2)/4 as h -> 0 (Eqs. 5-11)."""
+    f = 60e6
+    F = orc.analytic_field(orc.NEWKIRK, 1.0, 10.0, te0=1e6)
+    r0 = np.array([1.3, 0.5, 0.7])
+    rr = np.linalg.norm(r0)
+    khat = np.array([-0.6, 0.64, 0.48])
+    khat /= np.linalg.norm(khat)
+    k0 = _newkirk_n(rr, f) * khat
+    # n^2 = 1 - a 10^(b/r): g' and g'' in closed form
+    a = orc.c_pe() * 4.2e4 / f ** 2
+    bb = 4.32 * math.log(10)
+    ex = a * math.exp(bb / rr)
+    g1 = ex * bb / rr ** 2
+    g2 = -ex * (bb / rr ** 2) ** 2 - 2 * ex * bb / rr ** 3
+    c = (r0 / rr) @ khat
+    trp = g2 * (1 - c * c) + g1 / rr * (1 + c * c)
+    lim = trp / 4
+    errs = []
+    for h in (2e-3, 1e-3, 5e-4):
+        m = orc.stepwise_m(F, f, orc.default_options(dtau=h, n_nb=n_nb), r0, k0)
+        errs.append(abs((m - 1) / h ** 2 - lim))
+    assert errs[2] < 0.02 * abs(lim)
+    assert errs[2] < errs[1] < errs[0]
+
+
+# --------------------------------------------------------------- interpolant
+
+def test_interpolant_reproduces_linear_field(orc):
+    """Inside a cell the trilinear interpolant is exact for A + B r + C theta +
+    D phi, and its gradient is B r_hat + C theta_hat / r + D phi_hat / (r sin theta)."""
+    g = cs.newkirk_grid(10, 9, 12, 4.0)
+    R, T, P = np.meshgrid(g.r, g.theta, g.phi, indexing="ij")
+    A, B, Cc, D = 3.0e6, 2.0e5, -4.0e5, 1.5e5
+    g.ne = A + B * R + Cc * T + D * P
+    F = orc.grid_field(g)
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        r = rng.uniform(g.r[1], g.r[-2])
+        th = rng.uniform(g.theta[0] + 0.05, g.theta[-1] - 0.05)
+        ph = rng.uniform(0.05, g.phi[-1] - 0.05)
+        p = r * np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+        ne, grad, te = orc.field_eval(F, p)
+        assert ne == pytest.approx(A + B * r + Cc * th + D * ph, rel=1e-12)
+        rh = p / r
+        thh = np.array([math.cos(th) * math.cos(ph), math.cos(th) * math.sin(ph), -math.sin(th)])
+        phh = np.array([-math.sin(ph), math.cos(ph), 0.0])
+        expect = B * rh + Cc * thh / r + D * phh / (r * math.sin(th))
+        np.testing.assert_allclose(grad, expect, rtol=1e-9, atol=1e-6)
+
+
+def test_interpolant_gradient_matches_finite_differences(orc):
+    rng = np.random.default_rng(1)
+    g = cs.newkirk_grid(10, 9, 12, 4.0)
+    g.ne = g.ne * (1 + 0.5 * rng.random(g.ne.shape))
+    F = orc.grid_field(g)
+    for _ in range(40):
+        p = rng.normal(size=3)
+        p *= rng.uniform(1.1, 3.8) / np.linalg.norm(p)
+        ne, grad, _ = orc.field_eval(F, p)
+        h = 1e-6
+        fd = np.array([(orc.field_eval(F, p + h * e)[0] - orc.field_eval(F, p - h * e)[0]) / (2 * h)
+                       for e in np.eye(3)])
+        # skip the rare point within h of a cell face
+        if np.allclose(fd, grad, rtol=1e-5, atol=1e-3 * np.abs(grad).max()):
+            continue
+        pytest.fail(f"gradient {grad} vs FD {fd} at {p}")
+
+
+def test_phi_periodic_wrap(orc):
+    g = cs.newkirk_grid(6, 6, 8, 4.0)
+    g.ne = np.zeros_like(g.ne)
+    g.ne[:, :, 0] = 1e8
+    F = orc.grid_field(g)
+    dphi = 2 * math.pi / 8
+    th = g.theta[2] + 0.01
+    for frac in (0.25, 0.5, 0.75):
+        ph = 2 * math.pi - dphi + frac * dphi
+        p = 2.0 * np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+        ne, _, _ = orc.field_eval(F, p)
+        assert ne == pytest.approx(1e8 * frac, rel=1e-9)
+
+
+# ------------------------------------------------------------------ adjoint
+
+def test_adjoint_matches_central_differences(orc):
+    """Tape reverse-mode gradient of sum(w * T_b) against FP64 central FD."""
+    rng = np.random.default_rng(7)
+    g = cs.newkirk_grid(10, 8, 12, 4.0)
+    g.ne = g.ne * (1 + 0.2 * rng.random(g.ne.shape))
+    g.te = g.te * (1 + 0.3 * rng.random(g.ne.shape))
+    v = cs.View(0.3, 0.1, 4, 4, -1.5, 1.5, -1.5, 1.5)
+    freqs = [70e6, 250e6]
+    opts = orc.default_options(dtau=1e-2)
+    w = rng.normal(size=(2, 16))
+    gne, gte, tb = orc.backward(orc.grid_field(g), v, freqs, w, opts)
+
+    def loss(gg):
+        return float(np.sum(w * orc.trace(orc.grid_field(gg), v, freqs, opts)["tb"]))
+
+    assert np.allclose(tb, orc.trace(orc.grid_field(g), v, freqs, opts)["tb"], rtol=1e-13)
+    flat_ne = np.argsort(-np.abs(gne).ravel())[:12]
+    flat_te = np.argsort(-np.abs(gte).ravel())[:6]
+    checked = 0
+    for arr_name, flat, grad in (("ne", flat_ne, gne), ("te", flat_te, gte)):
+        for idx in flat:
+            base = getattr(g, arr_name)
+            hstep = 1e-5 * base.ravel()[idx]
+            plus = base.copy(); plus.ravel()[idx] += hstep
+            minus = base.copy(); minus.ravel()[idx] -= hstep
+            gp = cs.Grid(g.r, g.theta, g.phi, plus if arr_name == "ne" else g.ne, plus if arr_name == "te" else g.te)
+            gm = cs.Grid(g.r, g.theta, g.phi, minus if arr_name == "ne" else g.ne, minus if arr_name == "te" else g.te)
+            fd = (loss(gp) - loss(gm)) / (2 * hstep)
+            ad = grad.ravel()[idx]
+            assert abs(fd - ad) <= 1e-5 * abs(ad) + 1e-12, (arr_name, idx, fd, ad)
+            checked += 1
+    assert checked == 18
+
+
+def test_transfer_matches_formal_solution(orc):
+    """Straight line of sight (no refraction, no tube) through a grid whose
+    n_e and T_e vary along the chord: the discrete transfer (trapezoidal
+    optical depth, segment-mean T_e, Eq. 2 without the S term) converges at
+    second order to the formal solution int kappa T e^-tau ds + T_bc e^-tau(L)."""
+    from scipy.integrate import solve_ivp
+    rng = np.random.default_rng(11)
+    g = cs.newkirk_grid(24, 12, 16, 4.0)
+    R, T, P = np.meshgrid(g.r, g.theta, g.phi, indexing="ij")
+    g.ne = g.ne * (1 + 0.3 * np.sin(2 * T) * np.cos(P))
+    g.te = 1e6 * (1 + 0.5 * np.cos(T) + 0.2 * (R - 1) + 0.1 * rng.random(g.te.shape))
+    F = orc.grid_field(g)
+    f = 300e6
+    v = cs.View(0.2, 0.1, 3, 3, -1.4, 1.4, -1.4, 1.4)
+    rsun = orc.r_sun_cm()
+    o, eu, ev = frame(0.2, 0.1)
+    errs = {}
+    for h in (4e-3, 2e-3):
+        res = orc.trace(F, v, [f], orc.default_options(straight=1, s_mode=orc.MAG_OFF, dtau=h))
+        errs[h] = []
+        for pix in range(9):
+            u, w = pixel_uv(v, pix)
+            b2 = u * u + w * w
+            r0 = u * eu + w * ev + math.sqrt(16 - b2) * o
+            hit = b2 < 1.0
+            L = math.sqrt(16 - b2) - math.sqrt(1 - b2) if hit else 2 * math.sqrt(16 - b2)
+
+            def rhs(s, y):
+                ne, _, te = orc.field_eval(F, r0 - s * o)
+                kap = orc.kappa_vac(ne, te, f) * rsun
+                return [kap, kap * te * math.exp(-y[0])]
+            sol = solve_ivp(rhs, (0.0, L), [0.0, 0.0], rtol=1e-11, atol=1e-6, max_step=0.01)
+            tau_L, tb = sol.y[0, -1], sol.y[1, -1]
+            if hit:
+                tb += orc.field_eval(F, r0 - L * o)[2] * math.exp(-tau_L)
+            # trapezoidal tau: second order, with O(h^2) kinks at cell faces
+            assert res["tau"][0, pix] == pytest.approx(tau_L, rel=5e-4)
+            errs[h].append(abs(res["tb"][0, pix] / tb - 1))
+    assert max(errs[2e-3]) < 3e-6
+    # second order (a node-value source function would be first order and
+    # leave ~1e-3): halving the step cuts the error about 3-4x
+    assert max(errs[2e-3]) < 0.5 * max(errs[4e-3])
+
+
+def test_stepwise_eps_at_slab_surface(orc):
+    """A ray running parallel to a slab surface at depth d < eps: the -e2
+    neighbour starts in the force-free half space, the others in the constant
+    force -A z.  Then d_2 = eps e2 - (h^2 A / 4) z and M = 1 - h^2 A / (4 eps)
+    with eps = eta |dr| (Eq. 8): M - 1 is inversely proportional to eps."""
+    f, ne0 = F100, 1e8
+    F = orc.analytic_field(orc.SLAB, 0.05, 4.0, ne0=ne0, te0=1e6, q=(0.0, 0.0, 1.0), c=0.0)
+    A = orc.c_pe() * ne0 / (2 * f * f)
+    h = 2e-3
+    for eta in (0.5, 0.25):
+        d = 0.3 * eta * h
+        n = math.sqrt(1 - 2 * A * d)
+        r0 = np.array([0.5, 0.2, d])
+        k0 = n * np.array([-1.0, 0.0, 0.0])
+        dr = h * k0 + 0.5 * h * h * np.array([0.0, 0.0, -A])  # exact parabola step
+        eps = eta * np.linalg.norm(dr)
+        m = orc.stepwise_m(F, f, orc.default_options(dtau=h, eta=eta, n_nb=4), r0, k0)
+        assert (m - 1) == pytest.approx(-h * h * A / (4 * eps), rel=2e-3)
