@@ -1,0 +1,308 @@
+"""Benchmark: ray-steps/s and maps/s of the GB300 ray tracer.
+
+Workload (N = 1): the 256(r, 1-30 R_sun stretched) x 180(theta) x 360(phi)
+MAS-like synthetic corona, a 512x512 image over +-3 R_sun at 16 frequencies
+log-spaced 40-800 MHz, one ray bundle (central ray + 4 step-wise neighbours)
+per pixel and frequency, RK4 step 2e-3 R_sun, free-free transfer with the
+magnification term, compensated (mixed) form.  One step = one rt_trace_image
+call over the whole workload (16 maps, 4.19 M ray bundles).
+
+With N > 1 ranks (torchrun) every rank traces its own independent copy of the
+workload (observer longitude offset by rank): weak scaling, no data-path
+collective; `value` is the ray-steps of all ranks over the slowest rank's time.
+
+--impl reference runs the FP64 CPU oracle (the only reference arm this
+method has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ray-steps/s & maps/s (512^2 x 16 freq, 1 GB300); adjoint/forward time ratio"
+R_SUN_UNITS = "R_sun"
+
+# Algorithmic FP32 operations (FMA = 2) of the kernel's operation list:
+# one field evaluation (radius and cell lookup, two arctangents, trilinear
+# value and three partials, Cartesian chain rule) = 111; one RK4 lane-step =
+# 4 evaluations + 60; per central step the bookkeeping (tube area, basis,
+# transfer, termination) = 120 and the stage-1 T_e interpolation = 15.
+FLOP_EVAL = 111
+FLOP_RK4_EXTRA = 60
+FLOP_STEP_BOOK = 135
+
+
+def flops_per_ray_step(n_nb: int) -> int:
+    lanes = n_nb + 1
+    return lanes * (4 * FLOP_EVAL + FLOP_RK4_EXTRA) + FLOP_STEP_BOOK
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def shard_views(base_view, world_size: int, rank: int):
+    """Weak scaling: rank r traces the base image seen from longitude
+    lon + 2 pi r / world_size (independent problems, no shared output)."""
+    import corona_synth as cs
+    v = base_view
+    return cs.View(v.lon_rad + 2.0 * math.pi * rank / max(world_size, 1), v.lat_rad, v.nx, v.ny,
+                   v.x0, v.x1, v.y0, v.y1)
+
+
+def cpu_baseline(g, v, f, target_s=12.0, max_pixels=4096):
+    """The FP64 oracle (as it stands) on a bounded pixel sample of the same
+    workload, on this host's cores; ray-steps/s and the sample description."""
+    import oracle
+    F = oracle.grid_field(g)
+    opts = oracle.default_options(tau_stop=30.0)
+    rng = np.random.default_rng(12345)
+    cores = os.cpu_count() or 1
+    n = 16
+    total_steps, elapsed, used = 0, 0.0, 0
+    while elapsed < target_s and used < max_pixels:
+        pix = rng.choice(v.nx * v.ny, size=n, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        r = oracle.trace(F, v, f, opts, pixels=pix, nthreads=cores)
+        dt = time.perf_counter() - t0
+        total_steps += int(r["steps"].sum())
+        elapsed += dt
+        used += n
+        n = min(max(int(n * max(target_s - elapsed, 0.5) / max(dt, 1e-3) / 2), 16), max_pixels - used)
+        if n <= 0:
+            break
+    return {"value": total_steps / elapsed, "unit": "ray-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{used} random pixels x {len(f)} frequencies of the 512^2 workload "
+                      f"({total_steps} ray-steps in {elapsed:.1f} s, FP64, OpenMP over rays)"}
+
+
+def run_reference(args):
+    import corona_synth as cs
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    g, v, f = cs.global_workload(device="cpu")
+    # each step: a bounded sample of the workload through the oracle
+    times, steps = [], []
+    for i in range(args.warmup + args.steps):
+        res = cpu_baseline(g, v, f, target_s=max(4.0, 40.0 / max(args.steps, 1)), max_pixels=64)
+        if i >= args.warmup:
+            times.append(res)
+    val = float(np.mean([t["value"] for t in times]))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "ray-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "MAS-like 256x180x360 corona, 512x512 x 16 freq 40-800 MHz, 4 neighbours"},
+            "cpu_baseline": {"value": val, "unit": "ray-steps/s", "cores": times[0]["cores"], "kind": "oracle",
+                             "sample": times[0]["sample"]},
+            "e2e": {"value": val, "unit": "ray-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "plain"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import corona_synth as cs
+    from paper_2606_02413_gb300 import build as rt_build
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    rt_build.build()
+    import paper_2606_02413_gb300 as rt
+
+    g, v0, f = cs.global_workload()
+    v = shard_views(v0, ws, rank)
+    ctx = rt.Context(local)
+    grid = ctx.load(g)
+    prec = rt.RT_MIXED if args.precision == "mixed" else rt.RT_PLAIN_F32
+    opts = rt.options(precision=prec)
+    stream = torch.cuda.current_stream()
+    out = torch.empty((len(f), v.ny, v.nx), dtype=torch.float32, device=f"cuda:{local}")
+
+    for _ in range(args.warmup):
+        ctx.trace_image(grid, v, f, opts, out=out)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ray_steps = 0
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for e0, e1 in ev:
+        e0.record(stream)
+        ctx.trace_image(grid, v, f, opts, out=out)
+        e1.record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    stats = ctx.stats()  # counters of the last timed step (every step traces the same rays)
+    ray_steps = stats["ray_steps"] * args.steps
+    total_ms = t_start.elapsed_time(t_end)
+    kern_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    t = torch.tensor([total_ms], dtype=torch.float64)
+    steps_t = torch.tensor([float(ray_steps)], dtype=torch.float64)
+    if ws > 1:
+        t = t.cuda()
+        steps_t = steps_t.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(steps_t, op=dist.ReduceOp.SUM)
+    total_ms = float(t.item())
+    all_steps = float(steps_t.item())
+    value = all_steps / (total_ms / 1e3)
+    maps_per_s = len(f) * ws * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API: pinned host grid -> rt_load_grid ->
+    # rt_trace_image -> T_b maps back to pinned host memory, every step
+    e2e = None
+    if not args.no_e2e:
+        ne_h = torch.from_numpy(g.ne).pin_memory()
+        te_h = torch.from_numpy(g.te).pin_memory()
+        tb_h = torch.empty(out.shape, dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_e2e = 1
+        for _ in range(n_e2e):
+            gr = ctx.load_grid(g.r, g.theta, g.phi, ne_h.numpy(), te_h.numpy())
+            ctx.trace_image(gr, v, f, opts, out=out)
+            tb_h.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+            gr.free()
+        dt = (time.perf_counter() - t0) / n_e2e
+        e2e = {"value": stats["ray_steps"] * ws / dt, "unit": "ray-steps/s",
+               "h2d_bytes_per_step": int(ne_h.numel() * 4 + te_h.numel() * 4),
+               "d2h_bytes_per_step": int(tb_h.numel() * 4), "seconds_per_step": dt}
+
+    peaks, peak_src = load_peaks()
+    clk = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = 2.0 * 128 * n_sm * clk * 1e6 / 1e12  # TFLOP/s: 128 FP32 lanes x FMA per SM per clock
+    flop_step = flops_per_ray_step(4)
+    kmean = float(np.mean(kern_ms))
+    achieved = flop_step * stats["ray_steps"] / (kmean / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": None,
+            "peak_source": f"FP32 FMA: 128 lanes x {n_sm} SMs x 2 x {clk:.0f} MHz median SM clock under load",
+            "flop_per_ray_step": flop_step, "kernel": "trace_bundles<4, mixed>", "kernel_ms": kmean}
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = cpu_baseline(g, v0, f)
+        line = {"metric": METRIC, "value": value, "unit": "ray-steps/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "MAS-like synthetic corona 256(r, 1-30 R_sun) x 180 x 360, FP32 fields; "
+                                       "512x512 image +-3 R_sun x 16 freq log 40-800 MHz; step-wise tube, "
+                                       "4 neighbours, RK4 h = 2e-3 R_sun",
+                           "precision": args.precision, "maps_per_step": len(f) * ws,
+                           "rays_per_step": int(stats["rays"]) * ws, "l2": "inputs larger than L2 "
+                           "(1.06 GB corner-packed grid, 4.19 M rays/step)", "parallelism": f"weak x{ws}"},
+                "maps_per_s": maps_per_s, "ray_steps_per_step": all_steps / args.steps,
+                "adjoint_forward_ratio": None, "gpu_launches": args.steps,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "peaks_source": peak_src}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

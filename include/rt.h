@@ -1,0 +1,187 @@
+/*
+ * librt — GB300 (sm_103a) refractive radio ray tracing with ray-tube
+ * magnification and thermal free-free transfer.
+ *
+ * The library computes the method of "Modeling the Thermal Low-Frequency
+ * Radio Sun with Ray Tracing" (arXiv 2606.02413):
+ *   - rays from the observer through a spherical (r, theta, phi) grid of
+ *     electron density n_e and temperature T_e (Sec. 3.1-3.2), one ray per
+ *     image pixel and frequency;
+ *   - unmagnetised Hamiltonian ray equations dr/dtau = k, dk/dtau =
+ *     grad(n^2)/2 with n^2 = 1 - f_pe^2/f^2, advanced by RK4 with a fixed
+ *     step (Sec. 2.1, Eq. 4);
+ *   - the ray-tube area S(s) from step-wise perturbation retracing of
+ *     neighbour rays (Sec. 2.1, Eqs. 5-11);
+ *   - the transfer equation dI/ds = j - kappa I - I dlnS/ds (Eqs. 2-3,
+ *     12) with thermal free-free j and kappa, integrated along each ray.
+ *
+ * Units: lengths in solar radii (R_sun = 6.957e10 cm), frequencies in Hz,
+ * n_e in cm^-3, temperatures in K, brightness temperature T_b in K.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns rt_status: RT_OK (0) or a negative error code.
+ *     Nothing throws across the ABI.  rt_last_error() returns a message for
+ *     the calling thread's most recent failure.
+ *   - Argument errors are reported synchronously, before any work is queued.
+ *   - Work is queued on the caller's CUDA stream (passed as void*, a
+ *     cudaStream_t; NULL = the legacy default stream) and runs
+ *     asynchronously; device-side errors surface in rt_sync().
+ *   - Pointers documented "device" must be device (or managed) memory of the
+ *     context's device; "host" pointers are read before the call returns.
+ *   - Physically odd inputs are not errors: a frequency below the local
+ *     plasma frequency only makes rays turn earlier.
+ */
+#ifndef RT_H
+#define RT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int rt_status;
+enum {
+  RT_OK = 0,
+  RT_ERR_ARG = -1,      /* invalid argument (null pointer, bad size, bad option) */
+  RT_ERR_GRID = -2,     /* grid descriptor or grid values rejected               */
+  RT_ERR_CUDA = -3,     /* a CUDA runtime call failed                            */
+  RT_ERR_OOM = -4,      /* device allocation failed                              */
+  RT_ERR_TIMEOUT = -5,  /* a bounded device wait expired                         */
+  RT_ERR_CHECKED = -6,  /* a device-side bounds check recorded a violation       */
+  RT_ERR_UNSUPPORTED = -7 /* valid request this build does not implement        */
+};
+
+enum { RT_F32 = 0, RT_F64 = 1 };                       /* grid value types        */
+enum { RT_STEPWISE = 0, RT_TUBE = 1, RT_MAG_OFF = 2 }; /* ray-tube area mode      */
+enum { RT_PLAIN_F32 = 0, RT_MIXED = 1 };               /* arithmetic form         */
+
+/* Per-ray status (rt_ray_diag.status). */
+enum {
+  RT_RAY_EXIT_OUTER = 1, /* left the outer sphere moving outward              */
+  RT_RAY_HIT_INNER = 2,  /* reached the inner sphere r = r_min                */
+  RT_RAY_TAU_STOP = 3,   /* optical depth reached tau_stop                    */
+  RT_RAY_STEP_LIMIT = 4, /* max_steps central steps taken                     */
+  RT_RAY_MISS = 5,       /* line misses the outer sphere or cannot enter      */
+  RT_RAY_NAN = 6         /* state became non-finite                           */
+};
+
+typedef struct rt_ctx rt_ctx;
+typedef struct rt_grid rt_grid;
+
+/* Spherical grid (Sec. 3.1: n_e, T_e on an r x theta x phi mesh).
+ * r nodes: strictly increasing, r[0] > 0; r[0] and r[n_r-1] are the inner
+ *   and outer termination spheres.  Any spacing.
+ * theta nodes (colatitude, rad): strictly increasing in [0, pi], uniformly
+ *   spaced.  Outside [theta[0], theta[n_t-1]] the field is clamped.
+ * phi nodes (rad): uniformly spaced with n_p * dphi = 2 pi (periodic).
+ * Values ne, te: [n_r][n_t][n_p], phi fastest; ne >= 0, te > 0, finite. */
+typedef struct {
+  int n_r, n_theta, n_phi;
+  const double* r_nodes;      /* host, n_r entries      */
+  const double* theta_nodes;  /* host, n_theta entries  */
+  const double* phi_nodes;    /* host, n_phi entries    */
+  int dtype;                  /* RT_F32 or RT_F64 for ne and te            */
+  int on_device;              /* 1: ne/te are device pointers, 0: host     */
+} rt_grid_desc;
+
+/* Observer view (Sec. 3.2).  The observer direction is
+ * o = (cos lat cos lon, cos lat sin lon, sin lat); rays travel along -o.
+ * Image axes e_u = (-sin lon, cos lon, 0), e_v = o x e_u; pixel (ix, iy)
+ * sits at u = x0 + (ix + 1/2)(x1 - x0)/nx, v = y0 + (iy + 1/2)(y1 - y0)/ny. */
+typedef struct {
+  double lon_rad, lat_rad;
+  int nx, ny;
+  double x0, x1, y0, y1;
+} rt_view;
+
+typedef struct {
+  double dtau;      /* fixed RK4 step of the Hamiltonian parameter [R_sun] (> 0)   */
+  int s_mode;       /* RT_STEPWISE (paper), RT_TUBE, RT_MAG_OFF                     */
+  int n_nb;         /* neighbour rays: 2 (paper, one-sided), 4 or 8                 */
+  int eps_mode;     /* 0: eps = eta |dr| (Eq. 8); 1: eps = delta                    */
+  double eta;       /* perturbation ratio (Eq. 8)                                   */
+  double delta;     /* fixed offset [R_sun]                                         */
+  double tau_stop;  /* stop a ray once its optical depth reaches this (<= 0: never) */
+  int max_steps;    /* central steps per ray; <= 0: ceil(40 r_max / dtau)           */
+  int tbc_mode;     /* 0: inner boundary T_bc = T_e at the crossing; 1: tbc_K        */
+  double tbc_K;
+  int emission;     /* 1: free-free j and kappa; 0: j = kappa = 0 (I S = const)     */
+  int straight;     /* 1: straight lines of sight, n = 1, no magnification           */
+  int precision;    /* RT_PLAIN_F32 or RT_MIXED (compensated state and accumulators) */
+} rt_options;
+
+/* Optional per-ray diagnostics (28 bytes). */
+typedef struct {
+  float exit_pos[3]; /* last path node: crossing point for EXIT/HIT, else last node */
+  float tau;         /* optical depth along the path                               */
+  float ln_s;        /* ln(S_N / S_0)                                              */
+  int32_t steps;     /* central RK4 steps                                           */
+  int32_t status;    /* RT_RAY_*                                                    */
+} rt_ray_diag;
+
+/* Counters of the most recent trace call on a context. */
+typedef struct {
+  unsigned long long ray_steps;  /* central RK4 steps summed over rays               */
+  unsigned long long rays;       /* rays traced (MISS included)                      */
+} rt_stats;
+
+/* Fills *o with the defaults: dtau 2e-3, step-wise, 4 neighbours, eta 0.5,
+ * delta 1e-3, tau_stop 30, max_steps auto, T_bc = T_e, emission on, plain FP32. */
+void rt_default_options(rt_options* o);
+
+const char* rt_status_string(rt_status s);
+/* Message of the calling thread's last failed call ("" if none). */
+const char* rt_last_error(void);
+
+/* Creates a context on CUDA device `device`; *out owns a few KB of device
+ * scratch (queue counter, statistics).  Errors: RT_ERR_ARG, RT_ERR_CUDA. */
+rt_status rt_create(rt_ctx** out, int device);
+/* Releases the context and its scratch.  Grids must be freed first. */
+rt_status rt_destroy(rt_ctx* ctx);
+
+/* Copies the grid into library-owned device memory, converted to FP32 and
+ * repacked cell by cell (the 8 corner values of each cell contiguous, for
+ * n_e and T_e), and builds the radial lookup table.  Synchronous: returns
+ * after the copy and a device-side value check; the caller may free ne/te
+ * afterwards.  Errors: RT_ERR_ARG (null pointers), RT_ERR_GRID (node
+ * arrays not monotone / not uniform where required, non-finite or negative
+ * n_e, non-positive T_e), RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* desc, const void* ne, const void* te,
+                       void* stream, rt_grid** out);
+rt_status rt_free_grid(rt_ctx* ctx, rt_grid* grid);
+
+/* Traces one image at nf frequencies (Sec. 3.2-3.3): for every pixel and
+ * frequency one ray bundle (the central ray and its n_nb neighbours on
+ * adjacent lanes of a warp), stepped with RK4, with the tube magnification
+ * and the free-free transfer accumulated along the way.
+ * freqs_hz: host, nf entries (1 <= nf <= 64), each > 0.
+ * tb_out:   device, [nf][ny][nx] float, caller-owned, fully overwritten.
+ * diag:     device, [nf][ny][nx] rt_ray_diag, or NULL.
+ * Asynchronous on `stream`.  Errors: RT_ERR_ARG, RT_ERR_UNSUPPORTED,
+ * RT_ERR_CUDA. */
+rt_status rt_trace_image(rt_ctx* ctx, const rt_grid* grid, const rt_view* view,
+                         const double* freqs_hz, int nf, const rt_options* opt,
+                         float* tb_out, rt_ray_diag* diag, void* stream);
+
+/* Samples the interpolated corona at n points: the field evaluation of
+ * every RK4 stage (trilinear n_e, T_e in (r, theta, phi) and the exact
+ * Cartesian gradient of the n_e interpolant; Sec. 3.1-3.2, Eq. 4).
+ * xyz: device float [n][3] (R_sun).  out: device float [n][5] =
+ * (n_e, T_e, dn_e/dx, dn_e/dy, dn_e/dz), caller-owned.  n >= 0.
+ * Asynchronous on `stream`.  Errors: RT_ERR_ARG, RT_ERR_CUDA. */
+rt_status rt_probe_field(rt_ctx* ctx, const rt_grid* grid, const float* xyz, int n, float* out,
+                         void* stream);
+
+/* Waits for `stream` and reports device-side errors of earlier calls. */
+rt_status rt_sync(rt_ctx* ctx, void* stream);
+
+/* Reads the counters of the context's most recent trace call (waits for
+ * `stream`). */
+rt_status rt_get_stats(rt_ctx* ctx, void* stream, rt_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_H */

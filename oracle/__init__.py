@@ -46,7 +46,8 @@ class Options(C.Structure):
     _fields_ = [("dtau", C.c_double), ("s_mode", C.c_int), ("n_nb", C.c_int),
                 ("eps_mode", C.c_int), ("eta", C.c_double), ("delta", C.c_double),
                 ("tau_stop", C.c_double), ("max_steps", C.c_int), ("tbc_mode", C.c_int),
-                ("tbc_K", C.c_double), ("emission", C.c_int), ("straight", C.c_int)]
+                ("tbc_K", C.c_double), ("emission", C.c_int), ("straight", C.c_int),
+                ("jitter", C.c_double), ("jitter_seed", C.c_ulonglong)]
 
 
 class Ray(C.Structure):
@@ -90,7 +91,8 @@ def lib():
 
 def default_options(**kw) -> Options:
     o = Options(dtau=2e-3, s_mode=STEPWISE, n_nb=4, eps_mode=0, eta=0.5, delta=1e-3,
-                tau_stop=0.0, max_steps=0, tbc_mode=0, tbc_K=0.0, emission=1, straight=0)
+                tau_stop=0.0, max_steps=0, tbc_mode=0, tbc_K=0.0, emission=1, straight=0,
+                jitter=0.0, jitter_seed=1)
     for k, v in kw.items():
         setattr(o, k, v)
     return o

@@ -85,6 +85,22 @@ struct TapeNodes {
   }
 };
 
+// Conditioning probe (test instrument, off by default; not part of the
+// method): perturbs r, theta and phi of every field evaluation by a relative
+// amount of order `amp` from a counter-free xorshift stream, mimicking the
+// rounding of single-precision geometry.  Rays whose result moves a lot
+// under it are ill-conditioned at that precision.
+struct Jitter {
+  double amp = 0.0;
+  unsigned long long state = 0;
+  double next() {
+    state ^= state << 13;
+    state ^= state >> 7;
+    state ^= state << 17;
+    return ((state >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+  }
+};
+
 template <class T>
 struct Sample {
   T ne, te;
@@ -108,9 +124,11 @@ static int cell_index(const double* a, int n, double x) {
 // vacuum band; theta is clamped to the outermost nodes (no theta derivative
 // there); phi is periodic.
 template <class T, class Nodes>
-Sample<T> eval_field(const orc_field& F, const Nodes& nodes, const Vec3<T>& p) {
+Sample<T> eval_field(const orc_field& F, const Nodes& nodes, const Vec3<T>& p, Jitter* J = nullptr) {
   Sample<T> s{T(0.0), T(0.0), {T(0.0), T(0.0), T(0.0)}};
   T r = norm(p);
+  const bool jit = J && J->amp > 0.0 && F.kind == ORC_GRID;
+  if (jit) r = r * (1.0 + J->amp * J->next());
   if (val(r) > F.r_max * (1.0 + kOuterBand)) return s;  // vacuum
   switch (F.kind) {
     case ORC_VACUUM:
@@ -147,6 +165,10 @@ Sample<T> eval_field(const orc_field& F, const Nodes& nodes, const Vec3<T>& p) {
   T rho = sqrt(p.x * p.x + p.y * p.y);
   T th = atan2(rho, p.z);
   T ph = atan2(p.y, p.x) - F.phi[0];
+  if (jit) {
+    th = th + 3.0 * J->amp * J->next();
+    ph = ph + 3.0 * J->amp * J->next();
+  }
   const double two_pi = 2.0 * kPi;
   if (val(ph) < 0.0) ph = ph + two_pi;
   if (val(ph) >= two_pi) ph = ph - two_pi;
@@ -231,6 +253,7 @@ struct RayCtx {
   const orc_options* o;
   double f;
   double h;
+  Jitter* J = nullptr;
 };
 
 // dk/dtau = 1/2 grad n^2 = -(C_pe / 2 f^2) grad n_e  (Eq. 4 in the
@@ -238,7 +261,7 @@ struct RayCtx {
 template <class T, class Nodes>
 Vec3<T> force(const RayCtx& C, const Nodes& nodes, const Vec3<T>& p) {
   if (C.o->straight) return {T(0.0), T(0.0), T(0.0)};
-  Sample<T> s = eval_field<T>(*C.F, nodes, p);
+  Sample<T> s = eval_field<T>(*C.F, nodes, p, C.J);
   return scale(-kCpe / (2.0 * C.f * C.f), s.grad);
 }
 
@@ -345,7 +368,7 @@ bool launch(const RayCtx& C, const Nodes& nodes, const Frame& fr, double u, doub
     k0 = cvt<T>(fr.d);
     return true;
   }
-  Sample<T> s = eval_field<T>(*C.F, nodes, r0);
+  Sample<T> s = eval_field<T>(*C.F, nodes, r0, C.J);
   T n2 = 1.0 - kCpe * s.ne / (C.f * C.f);
   if (!(val(n2) > 0.0)) return false;
   k0 = scale(sqrt(n2), cvt<T>(fr.d));
@@ -418,7 +441,7 @@ Path<T> trace_path(const RayCtx& C, const Nodes& nodes, const Frame& fr, double 
   }
 
   auto sample = [&](const Vec3<T>& p) {
-    Sample<T> s = eval_field<T>(*C.F, nodes, p);
+    Sample<T> s = eval_field<T>(*C.F, nodes, p, C.J);
     P.ne.push_back(s.ne);
     P.te.push_back(s.te);
   };
@@ -623,7 +646,10 @@ int orc_trace(const orc_field* F, const orc_view* V, const double* freqs, int nf
   for (long t = 0; t < total; ++t) {
     const int fi = int(t / npix);
     const int px = pixels ? pixels[t % npix] : int(t % npix);
-    RayCtx C{F, o, freqs[fi], o->dtau};
+    Jitter J;
+    J.amp = o->jitter;
+    J.state = (o->jitter_seed ^ (0x9E3779B97F4A7C15ull * (unsigned long long)(t + 1))) | 1ull;
+    RayCtx C{F, o, freqs[fi], o->dtau, &J};
     PlainNodes nodes{F};
     PixelGeom g = pixel_centre(*V, px);
     Path<double> P = trace_path<double>(C, nodes, fr, g.u, g.v);

@@ -45,6 +45,10 @@ typedef struct {
   double tbc_K;
   int emission;     /* 1: free-free j, kappa; 0: j = kappa = 0                */
   int straight;     /* 1: straight line of sight (no refraction, n = 1)       */
+  double jitter;    /* conditioning probe (orc_trace only): relative noise    */
+                    /* of this size on r, theta, phi of every grid lookup;    */
+                    /* 0 = off (the method itself)                            */
+  unsigned long long jitter_seed;
 } orc_options;
 
 typedef struct {

@@ -1,0 +1,170 @@
+"""GB300-native refractive radio ray tracing (arXiv 2606.02413 hot path).
+
+Thin Python binding over the C ABI of ``librt.so`` (``include/rt.h``).  The
+functions here only marshal arguments: device memory and streams come from
+PyTorch, and every step of the ray tracing runs in librt's CUDA kernels.
+
+    ctx = Context(0)
+    grid = ctx.load_grid(r, theta, phi, ne, te)          # host numpy or CUDA tensors
+    tb = ctx.trace_image(grid, view, freqs, options(...))  # torch [nf, ny, nx] on the GPU
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _abi
+from ._abi import (RT_MAG_OFF, RT_MIXED, RT_PLAIN_F32, RT_STEPWISE, RT_TUBE, RAY_STATUS, RtError,
+                   check, lib)
+
+__all__ = ["Context", "Grid", "options", "view", "RtError", "RT_STEPWISE", "RT_TUBE", "RT_MAG_OFF",
+           "RT_PLAIN_F32", "RT_MIXED", "RAY_STATUS", "diag_to_numpy"]
+
+
+def options(**kw) -> _abi.Options:
+    """rt_options with the library defaults, overridden by keyword."""
+    o = _abi.Options()
+    lib().rt_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(f"rt_options has no field {k}")
+        setattr(o, k, v)
+    return o
+
+
+def view(v) -> _abi.View:
+    """rt_view from any object with lon_rad, lat_rad, nx, ny, x0, x1, y0, y1."""
+    if isinstance(v, _abi.View):
+        return v
+    return _abi.View(float(v.lon_rad), float(v.lat_rad), int(v.nx), int(v.ny), float(v.x0), float(v.x1),
+                     float(v.y0), float(v.y1))
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Grid:
+    """A library-owned device copy of a coronal grid (rt_grid)."""
+
+    def __init__(self, ctx: "Context", handle: C.c_void_p, shape):
+        self.ctx = ctx
+        self.handle = handle
+        self.shape = shape
+
+    def free(self):
+        if self.handle and self.ctx.handle:
+            check(lib().rt_free_grid(self.ctx.handle, self.handle), "rt_free_grid")
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """An rt_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        torch.cuda.init()
+        self.device = device
+        h = C.c_void_p()
+        check(lib().rt_create(C.byref(h), device), "rt_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib().rt_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----------------------------------------------------------- grids
+    def load_grid(self, r, theta, phi, ne, te, stream=None) -> Grid:
+        """rt_load_grid.  ne, te: [n_r, n_theta, n_phi] float32/float64, as
+        host numpy arrays or CUDA torch tensors (copied; caller keeps them)."""
+        import torch
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        if isinstance(ne, torch.Tensor):
+            assert ne.is_cuda and te.is_cuda and ne.dtype == te.dtype
+            ne, te = ne.contiguous(), te.contiguous()
+            dtype = _abi.RT_F64 if ne.dtype == torch.float64 else _abi.RT_F32
+            pne, pte, on_dev = ne.data_ptr(), te.data_ptr(), 1
+            shape = tuple(ne.shape)
+        else:
+            dt = np.float64 if np.asarray(ne).dtype == np.float64 else np.float32
+            ne = np.ascontiguousarray(ne, dtype=dt)
+            te = np.ascontiguousarray(te, dtype=dt)
+            dtype = _abi.RT_F64 if dt == np.float64 else _abi.RT_F32
+            pne, pte, on_dev = ne.ctypes.data, te.ctypes.data, 0
+            shape = ne.shape
+        desc = _abi.GridDesc(len(r), len(theta), len(phi), r.ctypes.data, theta.ctypes.data, phi.ctypes.data,
+                             dtype, on_dev)
+        h = C.c_void_p()
+        check(lib().rt_load_grid(self.handle, C.byref(desc), C.c_void_p(pne), C.c_void_p(pte),
+                                 _stream_ptr(stream), C.byref(h)), "rt_load_grid")
+        return Grid(self, h, shape)
+
+    def load(self, g, stream=None) -> Grid:
+        """rt_load_grid from a corona_synth.Grid-like object."""
+        return self.load_grid(g.r, g.theta, g.phi, g.ne, g.te, stream)
+
+    # ----------------------------------------------------------- tracing
+    def trace_image(self, grid: Grid, v, freqs, opts=None, out=None, diag=False, stream=None):
+        """rt_trace_image.  Returns T_b [nf, ny, nx] float32 on the GPU (and,
+        with diag=True, an int32 [nf, ny, nx, 7] tensor holding rt_ray_diag)."""
+        import torch
+        vs = view(v)
+        f = np.ascontiguousarray(np.atleast_1d(freqs), dtype=np.float64)
+        nf = len(f)
+        dev = torch.device("cuda", self.device)
+        if out is None:
+            out = torch.empty((nf, vs.ny, vs.nx), dtype=torch.float32, device=dev)
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+        assert out.numel() == nf * vs.ny * vs.nx
+        d = torch.empty((nf, vs.ny, vs.nx, 7), dtype=torch.int32, device=dev) if diag else None
+        o = opts if opts is not None else options()
+        check(lib().rt_trace_image(self.handle, grid.handle, C.byref(vs),
+                                   f.ctypes.data_as(C.POINTER(C.c_double)), nf, C.byref(o),
+                                   C.c_void_p(out.data_ptr()), C.c_void_p(d.data_ptr() if d is not None else 0),
+                                   _stream_ptr(stream)), "rt_trace_image")
+        return (out, d) if diag else out
+
+    def probe_field(self, grid: Grid, xyz, stream=None):
+        """rt_probe_field: (n_e, T_e, grad n_e) at points xyz [n, 3] -> [n, 5]."""
+        import torch
+        pts = torch.as_tensor(xyz, dtype=torch.float32).reshape(-1, 3).contiguous().to(f"cuda:{self.device}")
+        out = torch.empty((pts.shape[0], 5), dtype=torch.float32, device=pts.device)
+        check(lib().rt_probe_field(self.handle, grid.handle, C.c_void_p(pts.data_ptr()), pts.shape[0],
+                                   C.c_void_p(out.data_ptr()), _stream_ptr(stream)), "rt_probe_field")
+        return out
+
+    def sync(self, stream=None):
+        check(lib().rt_sync(self.handle, _stream_ptr(stream)), "rt_sync")
+
+    def stats(self, stream=None):
+        s = _abi.Stats()
+        check(lib().rt_get_stats(self.handle, _stream_ptr(stream), C.byref(s)), "rt_get_stats")
+        return {"ray_steps": int(s.ray_steps), "rays": int(s.rays)}
+
+
+def diag_to_numpy(d):
+    """Split an int32 [..., 7] rt_ray_diag tensor into numpy fields."""
+    a = d.cpu().numpy()
+    f = a.view(np.float32)
+    return {"exit": f[..., 0:3].astype(np.float64), "tau": f[..., 3].astype(np.float64),
+            "ln_s": f[..., 4].astype(np.float64), "steps": a[..., 5].astype(np.int64),
+            "status": a[..., 6].astype(np.int32)}

@@ -1,0 +1,506 @@
+// C-ABI host side of librt: contexts, grid loading and repacking, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rt.h"
+#include "rt_bundle.cuh"
+
+using namespace rt;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+// CODATA 2018, CGS: f_pe^2 = n_e e^2 / (pi m_e)
+constexpr double kElectronCharge = 4.803204712570263e-10;  // statC
+constexpr double kElectronMass = 9.1093837015e-28;         // g
+constexpr double kRsunCm = 6.957e10;                       // IAU nominal
+constexpr double kOuterBand = 1e-6;                        // vacuum beyond r_max (1 + band)
+
+thread_local std::string g_err;
+
+rt_status fail(rt_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define RT_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                   \
+    }                                                                                   \
+  } while (0)
+
+double c_pe() { return kElectronCharge * kElectronCharge / (kPi * kElectronMass); }
+
+int float_bits(float f) {
+  int i;
+  std::memcpy(&i, &f, sizeof i);
+  return i;
+}
+
+}  // namespace
+
+struct rt_ctx {
+  int device = 0;
+  int sm_count = 0;
+  unsigned int* d_counter = nullptr;        // work-queue ticket
+  unsigned long long* d_stats = nullptr;    // [2]
+};
+
+struct rt_grid {
+  GridDev dev{};
+  float4* ne = nullptr;
+  float4* te = nullptr;
+  int2* lut = nullptr;
+  float2* rcell = nullptr;
+  int n_r = 0, n_t = 0, n_p = 0;
+};
+
+// --------------------------------------------------------------- kernels
+namespace {
+
+template <class T>
+__global__ void pack_cells(const T* __restrict__ ne, const T* __restrict__ te, float4* cne, float4* cte,
+                           int n_r, int n_t, int n_p) {
+  const long ncell = (long)(n_r - 1) * (n_t - 1) * n_p;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncell; c += (long)gridDim.x * blockDim.x) {
+    const int k = (int)(c % n_p);
+    const long ij = c / n_p;
+    const int j = (int)(ij % (n_t - 1));
+    const int i = (int)(ij / (n_t - 1));
+    const int k1 = (k + 1 == n_p) ? 0 : k + 1;
+    float vn[8], vt[8];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        for (int cc = 0; cc < 2; ++cc) {
+          const long id = ((long)(i + a) * n_t + (j + b)) * n_p + (cc ? k1 : k);
+          vn[a * 4 + b * 2 + cc] = (float)ne[id];
+          vt[a * 4 + b * 2 + cc] = (float)te[id];
+        }
+    cne[2 * c] = make_float4(vn[0], vn[1], vn[2], vn[3]);
+    cne[2 * c + 1] = make_float4(vn[4], vn[5], vn[6], vn[7]);
+    cte[2 * c] = make_float4(vt[0], vt[1], vt[2], vt[3]);
+    cte[2 * c + 1] = make_float4(vt[4], vt[5], vt[6], vt[7]);
+  }
+}
+
+// Flags non-finite or negative n_e and non-finite or non-positive T_e.
+template <class T>
+__global__ void check_values(const T* __restrict__ ne, const T* __restrict__ te, long n, unsigned int* bad) {
+  unsigned int flag = 0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double a = (double)ne[i], b = (double)te[i];
+    if (!(a >= 0.0) || !std::isfinite(a)) flag |= 1u;
+    if (!(b > 0.0) || !std::isfinite(b)) flag |= 2u;
+  }
+  if (flag) atomicOr(bad, flag);
+}
+
+__global__ void probe_field(const GridDev G, const float* __restrict__ xyz, int n, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Sample s = eval_field<true>(G, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]);
+  out[5 * i] = s.ne;
+  out[5 * i + 1] = s.te;
+  out[5 * i + 2] = s.gx;
+  out[5 * i + 3] = s.gy;
+  out[5 * i + 4] = s.gz;
+}
+
+template <int NB, bool M>
+int blocks_per_sm() {
+  static int cached = -1;
+  if (cached < 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_bundles<NB, M>, kThreads, 0) != cudaSuccess || b < 1)
+      b = 1;
+    cached = b;
+  }
+  return cached;
+}
+
+template <int NB, bool M>
+cudaError_t launch_trace(const TraceParams& P, int sm_count, cudaStream_t s) {
+  const int grid = sm_count * blocks_per_sm<NB, M>();
+  trace_bundles<NB, M><<<grid, kThreads, 0, s>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t dispatch_trace(int nb, bool mixed, const TraceParams& P, int sm, cudaStream_t s) {
+  switch (nb) {
+    case 0: return mixed ? launch_trace<0, true>(P, sm, s) : launch_trace<0, false>(P, sm, s);
+    case 2: return mixed ? launch_trace<2, true>(P, sm, s) : launch_trace<2, false>(P, sm, s);
+    case 4: return mixed ? launch_trace<4, true>(P, sm, s) : launch_trace<4, false>(P, sm, s);
+    case 8: return mixed ? launch_trace<8, true>(P, sm, s) : launch_trace<8, false>(P, sm, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool strictly_increasing(const double* a, int n) {
+  for (int i = 0; i + 1 < n; ++i)
+    if (!(a[i + 1] > a[i]) || !std::isfinite(a[i]) || !std::isfinite(a[i + 1])) return false;
+  return true;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI
+extern "C" {
+
+void rt_default_options(rt_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->dtau = 2e-3;
+  o->s_mode = RT_STEPWISE;
+  o->n_nb = 4;
+  o->eps_mode = 0;
+  o->eta = 0.5;
+  o->delta = 1e-3;
+  o->tau_stop = 30.0;
+  o->max_steps = 0;
+  o->tbc_mode = 0;
+  o->tbc_K = 0.0;
+  o->emission = 1;
+  o->straight = 0;
+  o->precision = RT_PLAIN_F32;
+}
+
+const char* rt_status_string(rt_status s) {
+  switch (s) {
+    case RT_OK: return "RT_OK";
+    case RT_ERR_ARG: return "RT_ERR_ARG";
+    case RT_ERR_GRID: return "RT_ERR_GRID";
+    case RT_ERR_CUDA: return "RT_ERR_CUDA";
+    case RT_ERR_OOM: return "RT_ERR_OOM";
+    case RT_ERR_TIMEOUT: return "RT_ERR_TIMEOUT";
+    case RT_ERR_CHECKED: return "RT_ERR_CHECKED";
+    case RT_ERR_UNSUPPORTED: return "RT_ERR_UNSUPPORTED";
+    default: return "RT_ERR_UNKNOWN";
+  }
+}
+
+const char* rt_last_error(void) { return g_err.c_str(); }
+
+rt_status rt_create(rt_ctx** out, int device) {
+  if (!out) return fail(RT_ERR_ARG, "rt_create: out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  RT_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(RT_ERR_ARG, "rt_create: device %d of %d", device, ndev);
+  RT_CUDA(cudaSetDevice(device));
+  rt_ctx* c = new rt_ctx;
+  c->device = device;
+  cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, 64);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_stats, 64);
+  if (e != cudaSuccess) {
+    cudaFree(c->d_counter);
+    cudaFree(c->d_stats);
+    delete c;
+    return fail(RT_ERR_CUDA, "rt_create: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return RT_OK;
+}
+
+rt_status rt_destroy(rt_ctx* ctx) {
+  if (!ctx) return fail(RT_ERR_ARG, "rt_destroy: ctx is NULL");
+  cudaSetDevice(ctx->device);
+  cudaFree(ctx->d_counter);
+  cudaFree(ctx->d_stats);
+  delete ctx;
+  return RT_OK;
+}
+
+rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const void* te, void* stream,
+                       rt_grid** out) {
+  if (!ctx || !d || !ne || !te || !out) return fail(RT_ERR_ARG, "rt_load_grid: NULL argument");
+  *out = nullptr;
+  if (d->dtype != RT_F32 && d->dtype != RT_F64) return fail(RT_ERR_ARG, "rt_load_grid: dtype %d", d->dtype);
+  const int nr = d->n_r, nt = d->n_theta, np = d->n_phi;
+  if (nr < 2 || nt < 2 || np < 2) return fail(RT_ERR_GRID, "rt_load_grid: need >= 2 nodes per axis");
+  if (!d->r_nodes || !d->theta_nodes || !d->phi_nodes) return fail(RT_ERR_ARG, "rt_load_grid: NULL node array");
+  const long nodes = (long)nr * nt * np;
+  if ((long)(nr - 1) * (nt - 1) * np > (1L << 31) / 2) return fail(RT_ERR_GRID, "rt_load_grid: grid too large");
+  const double* R = d->r_nodes;
+  const double* T = d->theta_nodes;
+  const double* Ph = d->phi_nodes;
+  if (!strictly_increasing(R, nr) || !(R[0] > 0.0))
+    return fail(RT_ERR_GRID, "rt_load_grid: r nodes must be positive and strictly increasing");
+  if (!strictly_increasing(T, nt) || T[0] < 0.0 || T[nt - 1] > kPi + 1e-12)
+    return fail(RT_ERR_GRID, "rt_load_grid: theta nodes must increase strictly within [0, pi]");
+  const double dth = (T[nt - 1] - T[0]) / (nt - 1);
+  for (int j = 0; j < nt; ++j)
+    if (std::fabs(T[j] - (T[0] + j * dth)) > 1e-9)
+      return fail(RT_ERR_GRID, "rt_load_grid: theta nodes must be uniformly spaced");
+  if (!strictly_increasing(Ph, np)) return fail(RT_ERR_GRID, "rt_load_grid: phi nodes must increase strictly");
+  const double dph = 2.0 * kPi / np;
+  for (int k = 0; k < np; ++k)
+    if (std::fabs(Ph[k] - (Ph[0] + k * dph)) > 1e-9)
+      return fail(RT_ERR_GRID, "rt_load_grid: phi nodes must be uniform with n_phi * dphi = 2 pi");
+
+  // radial lookup: bins no wider than the narrowest cell hold at most one node
+  std::vector<float> Rf(nr);
+  for (int i = 0; i < nr; ++i) Rf[i] = (float)R[i];
+  double wmin = 1e300;
+  for (int i = 0; i + 1 < nr; ++i) wmin = std::min(wmin, (double)Rf[i + 1] - (double)Rf[i]);
+  if (!(wmin > 0)) return fail(RT_ERR_GRID, "rt_load_grid: r nodes collapse in FP32");
+  const double span = (double)Rf[nr - 1] - (double)Rf[0];
+  const double nb_d = std::ceil(span / wmin) + 1.0;
+  if (nb_d > (double)(1 << 22)) return fail(RT_ERR_GRID, "rt_load_grid: radial spacing too uneven for the lookup table");
+  const int nb = (int)nb_d;
+  const double bw = span / nb;
+  std::vector<int2> lut(nb);
+  for (int b = 0; b < nb; ++b) {
+    const double lo = (double)Rf[0] + b * bw, hi = lo + bw;
+    int base = (int)(std::upper_bound(Rf.begin(), Rf.end(), (float)lo) - Rf.begin()) - 1;
+    base = std::min(std::max(base, 0), nr - 2);
+    while (base > 0 && (double)Rf[base] > lo) --base;
+    float split = std::numeric_limits<float>::infinity();
+    if (base + 1 <= nr - 2 && (double)Rf[base + 1] < hi) split = Rf[base + 1];
+    lut[b] = make_int2(base, float_bits(split));
+  }
+  std::vector<float2> rcell(nr - 1);
+  for (int i = 0; i + 1 < nr; ++i)
+    rcell[i] = make_float2(Rf[i], (float)(1.0 / ((double)Rf[i + 1] - (double)Rf[i])));
+
+  RT_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  rt_grid* g = new rt_grid;
+  g->n_r = nr; g->n_t = nt; g->n_p = np;
+  const long ncell = (long)(nr - 1) * (nt - 1) * np;
+  const size_t esz = d->dtype == RT_F64 ? 8 : 4;
+  void* tmp_ne = nullptr;
+  void* tmp_te = nullptr;
+  unsigned int* d_bad = nullptr;
+  unsigned int h_bad = 0;
+  auto cleanup = [&](bool keep) {
+    if (d->on_device == 0) {
+      cudaFree(tmp_ne);
+      cudaFree(tmp_te);
+    }
+    cudaFree(d_bad);
+    if (!keep) {
+      cudaFree(g->ne); cudaFree(g->te); cudaFree(g->lut); cudaFree(g->rcell);
+      delete g;
+    }
+  };
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&g->ne, sizeof(float4) * 2 * ncell);
+  if (e == cudaSuccess) e = cudaMalloc(&g->te, sizeof(float4) * 2 * ncell);
+  if (e == cudaSuccess) e = cudaMalloc(&g->lut, sizeof(int2) * nb);
+  if (e == cudaSuccess) e = cudaMalloc(&g->rcell, sizeof(float2) * (nr - 1));
+  if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(unsigned int));
+  if (e == cudaSuccess && d->on_device == 0) {
+    e = cudaMalloc(&tmp_ne, esz * nodes);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp_te, esz * nodes);
+  }
+  if (e != cudaSuccess) {
+    cleanup(false);
+    return fail(e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "rt_load_grid: %s", cudaGetErrorString(e));
+  }
+  const void* src_ne = ne;
+  const void* src_te = te;
+  if (d->on_device == 0) {
+    e = cudaMemcpyAsync(tmp_ne, ne, esz * nodes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tmp_te, te, esz * nodes, cudaMemcpyHostToDevice, s);
+    src_ne = tmp_ne;
+    src_te = tmp_te;
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->lut, lut.data(), sizeof(int2) * nb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->rcell, rcell.data(), sizeof(float2) * (nr - 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned int), s);
+  const int blocks = ctx->sm_count * 8;
+  if (e == cudaSuccess) {
+    if (d->dtype == RT_F64) {
+      check_values<double><<<blocks, 256, 0, s>>>((const double*)src_ne, (const double*)src_te, nodes, d_bad);
+      pack_cells<double><<<blocks, 256, 0, s>>>((const double*)src_ne, (const double*)src_te, g->ne, g->te, nr, nt, np);
+    } else {
+      check_values<float><<<blocks, 256, 0, s>>>((const float*)src_ne, (const float*)src_te, nodes, d_bad);
+      pack_cells<float><<<blocks, 256, 0, s>>>((const float*)src_ne, (const float*)src_te, g->ne, g->te, nr, nt, np);
+    }
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, d_bad, sizeof h_bad, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cleanup(false);
+    return fail(RT_ERR_CUDA, "rt_load_grid: %s", cudaGetErrorString(e));
+  }
+  if (h_bad) {
+    cleanup(false);
+    return fail(RT_ERR_GRID, "rt_load_grid: %s%s", (h_bad & 1) ? "n_e must be finite and >= 0; " : "",
+                (h_bad & 2) ? "T_e must be finite and > 0" : "");
+  }
+  cleanup(true);
+
+  GridDev& G = g->dev;
+  G.ne = g->ne;
+  G.te = g->te;
+  G.r_lut = g->lut;
+  G.r_cell = g->rcell;
+  G.n_r = nr; G.n_t = nt; G.n_p = np;
+  G.r_lut_n = nb;
+  G.r_lut0 = Rf[0];
+  G.r_lut_inv = (float)(nb / span);
+  G.r_min = Rf[0];
+  G.r_max = Rf[nr - 1];
+  G.r_vac = (float)(R[nr - 1] * (1.0 + kOuterBand));
+  G.t0 = (float)T[0];
+  G.t_inv = (float)(1.0 / dth);
+  G.t_last = (float)(nt - 1);
+  G.p0 = (float)Ph[0];
+  G.p_inv = (float)(np / (2.0 * kPi));
+  *out = g;
+  return RT_OK;
+}
+
+rt_status rt_free_grid(rt_ctx* ctx, rt_grid* g) {
+  if (!ctx || !g) return fail(RT_ERR_ARG, "rt_free_grid: NULL argument");
+  cudaSetDevice(ctx->device);
+  cudaFree(g->ne);
+  cudaFree(g->te);
+  cudaFree(g->lut);
+  cudaFree(g->rcell);
+  delete g;
+  return RT_OK;
+}
+
+static rt_status check_options(const rt_options* o, int* nb_out) {
+  if (!o) return fail(RT_ERR_ARG, "options are NULL");
+  if (!(o->dtau > 0.0) || !std::isfinite(o->dtau)) return fail(RT_ERR_ARG, "dtau must be > 0");
+  if (o->s_mode != RT_STEPWISE && o->s_mode != RT_TUBE && o->s_mode != RT_MAG_OFF)
+    return fail(RT_ERR_ARG, "s_mode %d", o->s_mode);
+  if (o->n_nb != 2 && o->n_nb != 4 && o->n_nb != 8) return fail(RT_ERR_ARG, "n_nb must be 2, 4 or 8");
+  if (o->eps_mode == 0 && !(o->eta > 0.0)) return fail(RT_ERR_ARG, "eta must be > 0");
+  if (o->eps_mode == 1 && !(o->delta > 0.0)) return fail(RT_ERR_ARG, "delta must be > 0");
+  if (o->eps_mode != 0 && o->eps_mode != 1) return fail(RT_ERR_ARG, "eps_mode %d", o->eps_mode);
+  if (o->precision != RT_PLAIN_F32 && o->precision != RT_MIXED) return fail(RT_ERR_ARG, "precision %d", o->precision);
+  if (o->tbc_mode != 0 && o->tbc_mode != 1) return fail(RT_ERR_ARG, "tbc_mode %d", o->tbc_mode);
+  if (o->s_mode == RT_TUBE && !o->straight) return fail(RT_ERR_UNSUPPORTED, "tube mode is not built yet");
+  *nb_out = (o->straight || o->s_mode == RT_MAG_OFF) ? 0 : o->n_nb;
+  return RT_OK;
+}
+
+static rt_status check_view(const rt_view* v) {
+  if (!v) return fail(RT_ERR_ARG, "view is NULL");
+  if (v->nx < 1 || v->ny < 1) return fail(RT_ERR_ARG, "image size %d x %d", v->nx, v->ny);
+  if ((long)v->nx * v->ny > (1L << 30)) return fail(RT_ERR_ARG, "image too large");
+  if (!std::isfinite(v->lon_rad) || !std::isfinite(v->lat_rad) || !std::isfinite(v->x0) || !std::isfinite(v->x1) ||
+      !std::isfinite(v->y0) || !std::isfinite(v->y1))
+    return fail(RT_ERR_ARG, "view has non-finite fields");
+  return RT_OK;
+}
+
+rt_status rt_trace_image(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const double* freqs, int nf,
+                         const rt_options* o, float* tb_out, rt_ray_diag* diag, void* stream) {
+  if (!ctx || !g || !freqs || !tb_out) return fail(RT_ERR_ARG, "rt_trace_image: NULL argument");
+  rt_status st = check_view(v);
+  if (st != RT_OK) return st;
+  int nb = 0;
+  st = check_options(o, &nb);
+  if (st != RT_OK) return st;
+  if (nf < 1 || nf > kMaxFreq) return fail(RT_ERR_ARG, "rt_trace_image: nf = %d (1..%d)", nf, kMaxFreq);
+  for (int i = 0; i < nf; ++i)
+    if (!(freqs[i] > 0.0) || !std::isfinite(freqs[i])) return fail(RT_ERR_ARG, "frequency %d is not > 0", i);
+  const long total = (long)nf * v->nx * v->ny;
+  if (total >= (1L << 31)) return fail(RT_ERR_ARG, "rt_trace_image: too many rays");
+
+  TraceParams P;
+  std::memset(&P, 0, sizeof P);
+  P.G = g->dev;
+  const double h = o->dtau;
+  P.h = (float)h;
+  P.h2_6 = (float)(h * h / 6.0);
+  P.h_6 = (float)(h / 6.0);
+  P.h2_12 = (float)(h * h / 12.0);
+  P.hrsun = (float)(h * kRsunCm);
+  P.eta = (float)o->eta;
+  P.eps_fixed = o->eps_mode == 1 ? (float)o->delta : 0.f;
+  P.tau_stop = (float)o->tau_stop;
+  P.max_steps = o->max_steps > 0 ? o->max_steps : (int)std::ceil(40.0 * g->dev.r_max / h);
+  P.tbc_mode = o->tbc_mode;
+  P.tbc_K = (float)o->tbc_K;
+  P.emission = o->emission;
+  P.straight = o->straight;
+  const double cl = std::cos(v->lon_rad), sl = std::sin(v->lon_rad), cb = std::cos(v->lat_rad), sb = std::sin(v->lat_rad);
+  P.ox = (float)(cb * cl); P.oy = (float)(cb * sl); P.oz = (float)sb;
+  P.eux = (float)(-sl); P.euy = (float)cl; P.euz = 0.f;
+  P.evx = (float)(-sb * cl); P.evy = (float)(-sb * sl); P.evz = (float)cb;
+  P.x0 = (float)v->x0; P.dx = (float)((v->x1 - v->x0) / v->nx);
+  P.y0 = (float)v->y0; P.dy = (float)((v->y1 - v->y0) / v->ny);
+  P.nx = v->nx; P.ny = v->ny; P.npix = v->nx * v->ny;
+  P.nf = nf;
+  // lowest frequencies first: their rays turn high and tend to be longest
+  std::vector<int> order(nf);
+  for (int i = 0; i < nf; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return freqs[a] < freqs[b]; });
+  const double cpe = c_pe();
+  for (int i = 0; i < nf; ++i) {
+    const double f = freqs[order[i]];
+    P.freq[i].kf = (float)(-cpe / (2.0 * f * f));
+    P.freq[i].kn2 = (float)(-cpe / (f * f));
+    P.freq[i].kap_c = (float)(9.78e-3 / (f * f));
+    P.freq[i].ln_f = (float)std::log(f);
+    P.freq[i].out_slab = order[i];
+  }
+  P.tb_out = tb_out;
+  P.diag = reinterpret_cast<RayDiag*>(diag);
+  P.counter = ctx->d_counter;
+  P.stats = ctx->d_stats;
+  P.total = (unsigned int)total;
+
+  RT_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  RT_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), s));
+  RT_CUDA(cudaMemsetAsync(ctx->d_stats, 0, 2 * sizeof(unsigned long long), s));
+  RT_CUDA(dispatch_trace(nb, o->precision == RT_MIXED, P, ctx->sm_count, s));
+  return RT_OK;
+}
+
+rt_status rt_probe_field(rt_ctx* ctx, const rt_grid* g, const float* xyz, int n, float* out, void* stream) {
+  if (!ctx || !g || (n > 0 && (!xyz || !out))) return fail(RT_ERR_ARG, "rt_probe_field: NULL argument");
+  if (n < 0) return fail(RT_ERR_ARG, "rt_probe_field: n = %d", n);
+  if (n == 0) return RT_OK;
+  RT_CUDA(cudaSetDevice(ctx->device));
+  probe_field<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(g->dev, xyz, n, out);
+  RT_CUDA(cudaGetLastError());
+  return RT_OK;
+}
+
+rt_status rt_sync(rt_ctx* ctx, void* stream) {
+  if (!ctx) return fail(RT_ERR_ARG, "rt_sync: ctx is NULL");
+  RT_CUDA(cudaSetDevice(ctx->device));
+  RT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  RT_CUDA(cudaGetLastError());
+  return RT_OK;
+}
+
+rt_status rt_get_stats(rt_ctx* ctx, void* stream, rt_stats* out) {
+  if (!ctx || !out) return fail(RT_ERR_ARG, "rt_get_stats: NULL argument");
+  RT_CUDA(cudaSetDevice(ctx->device));
+  unsigned long long h[2] = {0, 0};
+  RT_CUDA(cudaMemcpyAsync(h, ctx->d_stats, sizeof h, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  RT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  out->ray_steps = h[0];
+  out->rays = h[1];
+  return RT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,290 @@
+// Device code of librt: field evaluation, RK4, and the warp-cooperative
+// ray-bundle kernel (Sec. 2.1 Eqs. 4-12, Sec. 3.2 of arXiv 2606.02413).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rt {
+
+constexpr float kTwoPiF = 6.28318530717958647692f;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxFreq = 64;
+constexpr int kThreads = 128;
+#ifndef RT_MIN_BLOCKS
+#define RT_MIN_BLOCKS 1
+#endif
+constexpr int kMinBlocks = RT_MIN_BLOCKS;  // __launch_bounds__ occupancy target
+
+// ------------------------------------------------------------------ grid
+// Cells are corner-packed: cell (i, j, k) stores the 8 node values of its
+// corners as two float4, corner index a*4 + b*2 + c for the (r, theta, phi)
+// offsets (a, b, c), so one evaluation is two 16-byte loads from one 32-byte
+// sector.  Cell k = n_phi - 1 wraps to node 0 (phi is periodic).
+struct GridDev {
+  const float4* ne;      // [cells][2]
+  const float4* te;      // [cells][2]
+  const int2* r_lut;     // radial bins: (cell at the bin's lower edge, bits of the node inside the bin or +inf)
+  const float2* r_cell;  // [n_r - 1]: (R_i, 1 / (R_{i+1} - R_i))
+  int n_r, n_t, n_p;
+  int r_lut_n;
+  float r_lut0, r_lut_inv;
+  float r_min, r_max, r_vac;  // r_vac = r_max (1 + 1e-6): beyond it, vacuum
+  float t0, t_inv, t_last;    // theta_0, 1 / dtheta, n_t - 1
+  float p0, p_inv;            // phi_0, n_p / (2 pi)
+};
+
+struct Sample {
+  float ne, te, gx, gy, gz;  // n_e, T_e, grad n_e
+};
+
+// atan2 for the grid lookup: the argument is reduced to a = min/max in [0, 1],
+// atan(a) = a P(a^2) with the degree-7 polynomial fitted by csrc/fit_atan.py
+// (max error 3.7e-8 in exact arithmetic, ~2e-7 rad after FP32 rounding), and
+// the quadrant of (x, y) restored.
+__device__ __forceinline__ float atan2_grid(float y, float x) {
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+  const float a = (mx > 0.f) ? __fdividef(mn, mx) : 0.f;
+  const float t = a * a;
+  float p = -4.054565173e-03f;
+  p = fmaf(p, t, 2.186295542e-02f);
+  p = fmaf(p, t, -5.591233286e-02f);
+  p = fmaf(p, t, 9.642198762e-02f);
+  p = fmaf(p, t, -1.390863067e-01f);
+  p = fmaf(p, t, 1.994656605e-01f);
+  p = fmaf(p, t, -3.332986085e-01f);
+  p = fmaf(p, t, 9.999993356e-01f);
+  float r = a * p;
+  if (ay > ax) r = 1.57079632679489662f - r;
+  if (x < 0.f) r = 3.14159265358979324f - r;
+  return copysignf(r, y);
+}
+
+// Trilinear interpolant in (r, theta, phi) (linear in physical r) and its
+// exact gradient chain-ruled to Cartesian:
+//   grad f = f_r r_hat + f_theta theta_hat / r + f_phi phi_hat / (r sin theta).
+template <bool kWantTe>
+__device__ __forceinline__ Sample eval_field(const GridDev& G, float x, float y, float z) {
+  Sample s;
+  const float rho2 = fmaf(x, x, y * y);
+  const float r2 = fmaf(z, z, rho2);
+  const float r = sqrtf(r2);
+  if (!(r <= G.r_vac)) {  // vacuum beyond the outer band (and NaN positions)
+    s.ne = 0.f; s.te = 0.f; s.gx = 0.f; s.gy = 0.f; s.gz = 0.f;
+    return s;
+  }
+  const float inv_r = __fdividef(1.0f, r);
+  // radial cell from the lookup table: at most one node lies inside a bin
+  int bin = __float2int_rd((r - G.r_lut0) * G.r_lut_inv);
+  bin = min(max(bin, 0), G.r_lut_n - 1);
+  const int2 e = __ldg(G.r_lut + bin);
+  const int i = min(e.x + (r >= __int_as_float(e.y) ? 1 : 0), G.n_r - 2);
+  const float2 rc = __ldg(G.r_cell + i);
+  const float u = (r - rc.x) * rc.y;
+
+  const float rho = sqrtf(rho2);
+  const float tt = (atan2_grid(rho, z) - G.t0) * G.t_inv;
+  int j;
+  float v, tsel;
+  if (tt > 0.f && tt < G.t_last) {
+    j = min(__float2int_rd(tt), G.n_t - 2);
+    v = tt - (float)j;
+    tsel = 1.f;
+  } else if (tt <= 0.f) {
+    j = 0; v = 0.f; tsel = 0.f;
+  } else {
+    j = G.n_t - 2; v = 1.f; tsel = 0.f;
+  }
+  float ph = atan2_grid(y, x) - G.p0;
+  if (ph < 0.f) ph += kTwoPiF;
+  if (ph >= kTwoPiF) ph -= kTwoPiF;
+  const float pp = ph * G.p_inv;
+  const int k = min(max(__float2int_rd(pp), 0), G.n_p - 1);
+  const float w = pp - (float)k;
+
+  const int cell = (i * (G.n_t - 1) + j) * G.n_p + k;
+  const float4 c0 = __ldg(G.ne + 2 * cell);      // (000, 001, 010, 011)
+  const float4 c1 = __ldg(G.ne + 2 * cell + 1);  // (100, 101, 110, 111)
+  const float d00 = c0.y - c0.x, d01 = c0.w - c0.z, d10 = c1.y - c1.x, d11 = c1.w - c1.z;
+  const float a00 = fmaf(w, d00, c0.x), a01 = fmaf(w, d01, c0.z);
+  const float a10 = fmaf(w, d10, c1.x), a11 = fmaf(w, d11, c1.z);
+  const float e0 = a01 - a00, e1 = a11 - a10;
+  const float b0 = fmaf(v, e0, a00), b1 = fmaf(v, e1, a10);
+  const float fu = b1 - b0;
+  s.ne = fmaf(u, fu, b0);
+  const float fv = fmaf(u, e1 - e0, e0);
+  const float g0 = fmaf(v, d01 - d00, d00), g1 = fmaf(v, d11 - d10, d10);
+  const float fw = fmaf(u, g1 - g0, g0);
+
+  const float f_r = fu * rc.y;
+  const float f_t = fv * G.t_inv * tsel;
+  const float f_p = fw * G.p_inv;
+  const float A = f_r * inv_r;
+  float B = 0.f, C = 0.f, D = 0.f;
+  if (rho2 > 0.f) {
+    const float inv_rho = __fdividef(1.0f, rho);
+    const float ir2 = inv_r * inv_r;
+    B = f_t * z * ir2 * inv_rho;  // theta term, x and y components (per x, y)
+    C = f_p * inv_rho * inv_rho;  // phi term
+    D = f_t * rho * ir2;          // theta term, z component
+  }
+  s.gx = fmaf(A + B, x, -C * y);
+  s.gy = fmaf(A + B, y, C * x);
+  s.gz = fmaf(A, z, -D);
+  if (kWantTe) {
+    const float4 t0 = __ldg(G.te + 2 * cell);
+    const float4 t1 = __ldg(G.te + 2 * cell + 1);
+    const float p00 = fmaf(w, t0.y - t0.x, t0.x), p01 = fmaf(w, t0.w - t0.z, t0.z);
+    const float p10 = fmaf(w, t1.y - t1.x, t1.x), p11 = fmaf(w, t1.w - t1.z, t1.z);
+    const float q0 = fmaf(v, p01 - p00, p00), q1 = fmaf(v, p11 - p10, p10);
+    s.te = fmaf(u, q1 - q0, q0);
+  } else {
+    s.te = 0.f;
+  }
+  return s;
+}
+
+// ------------------------------------------------------------------- RK4
+// One RK4 step of dr/dtau = k, dk/dtau = kf grad n_e (kf = -C_pe / (2 f^2),
+// i.e. grad(n^2)/2) from (p, k).  Returns G = a1 + a2 + a3 and
+// A = a1 + 2 a2 + 2 a3 + a4 so that
+//   r' = r + h k + h^2/6 G,   k' = k + h/6 A
+// (the textbook RK4 combination written in increment form), and the stage-1
+// sample at p.
+struct Rk4Out {
+  float Gx, Gy, Gz, Ax, Ay, Az;
+  float ne1, te1;
+};
+
+__device__ __forceinline__ Rk4Out rk4_step(const GridDev& G, float kf, float h, float px, float py,
+                                           float pz, float kx, float ky, float kz, bool want_te) {
+  Rk4Out o;
+  const float hh = 0.5f * h;
+  Sample s = want_te ? eval_field<true>(G, px, py, pz) : eval_field<false>(G, px, py, pz);
+  o.ne1 = s.ne;
+  o.te1 = s.te;
+  float ax = kf * s.gx, ay = kf * s.gy, az = kf * s.gz;
+  o.Gx = ax; o.Gy = ay; o.Gz = az;
+  o.Ax = ax; o.Ay = ay; o.Az = az;
+  // stage 2
+  float qx = fmaf(hh, ax, kx), qy = fmaf(hh, ay, ky), qz = fmaf(hh, az, kz);
+  s = eval_field<false>(G, fmaf(hh, kx, px), fmaf(hh, ky, py), fmaf(hh, kz, pz));
+  ax = kf * s.gx; ay = kf * s.gy; az = kf * s.gz;
+  o.Gx += ax; o.Gy += ay; o.Gz += az;
+  o.Ax = fmaf(2.f, ax, o.Ax); o.Ay = fmaf(2.f, ay, o.Ay); o.Az = fmaf(2.f, az, o.Az);
+  // stage 3
+  const float q3x = fmaf(hh, ax, kx), q3y = fmaf(hh, ay, ky), q3z = fmaf(hh, az, kz);
+  s = eval_field<false>(G, fmaf(hh, qx, px), fmaf(hh, qy, py), fmaf(hh, qz, pz));
+  ax = kf * s.gx; ay = kf * s.gy; az = kf * s.gz;
+  o.Gx += ax; o.Gy += ay; o.Gz += az;
+  o.Ax = fmaf(2.f, ax, o.Ax); o.Ay = fmaf(2.f, ay, o.Ay); o.Az = fmaf(2.f, az, o.Az);
+  // stage 4
+  s = eval_field<false>(G, fmaf(h, q3x, px), fmaf(h, q3y, py), fmaf(h, q3z, pz));
+  o.Ax = fmaf(kf, s.gx, o.Ax); o.Ay = fmaf(kf, s.gy, o.Ay); o.Az = fmaf(kf, s.gz, o.Az);
+  return o;
+}
+
+// --------------------------------------------------------- transfer bits
+struct FreqDev {
+  float kf;      // -C_pe / (2 f^2): dk/dtau = kf grad n_e
+  float kn2;     // -C_pe / f^2:     n^2 = 1 + kn2 n_e
+  float kap_c;   // 9.78e-3 / f^2
+  float ln_f;    // ln f
+  int out_slab;  // output slab of this frequency
+};
+
+// Free-free absorption coefficient in vacuum units [cm^-1] (Dulk 1985,
+// pure hydrogen): 9.78e-3 n_e^2 G / (f^2 T^1.5), G = 24.5 + ln T - ln f
+// (T > 2e5 K) or 18.2 + 1.5 ln T - ln f.
+__device__ __forceinline__ float kappa_vac(float ne, float te, const FreqDev& F) {
+  if (!(ne > 0.f) || !(te > 0.f)) return 0.f;
+  const float lnT = __logf(te);
+  const float g = (te > 2e5f) ? (24.5f + lnT - F.ln_f) : fmaf(1.5f, lnT, 18.2f - F.ln_f);
+  const float rs = rsqrtf(te);
+  return (F.kap_c * ne) * ne * g * (rs * rs * rs);
+}
+
+// 1 - e^-x for x >= 0: Taylor series below 0.05 (truncation < 1e-9
+// relative), else through the exponential (no cancellation there).
+__device__ __forceinline__ float one_minus_exp_neg(float x) {
+  if (x < 0.05f) {
+    const float t = fmaf(-x, 0.2f, 1.f);
+    const float u = fmaf(-x * 0.25f, t, 1.f);
+    const float v = fmaf(-x * (1.f / 3.f), u, 1.f);
+    return x * fmaf(-x * 0.5f, v, 1.f);
+  }
+  return 1.f - __expf(-x);
+}
+
+// ln(1 + m): series below |m| = 1e-2 (truncation < 2e-11), else the log.
+__device__ __forceinline__ float log1p_small(float m) {
+  if (fabsf(m) < 1e-2f) {
+    const float a = fmaf(-0.75f, m, 1.f);        // 1 - 3m/4
+    const float b = fmaf(-m * (2.f / 3.f), a, 1.f);
+    return m * fmaf(-0.5f * m, b, 1.f);          // m - m^2/2 + m^3/3 - m^4/4
+  }
+  return __logf(fabsf(1.f + m));
+}
+
+// Error-free sum a + b = s + e (Knuth TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Running sum.  kComp = true keeps the rounding error of every addition
+// (TwoSum) and carries it, so 10^4-term sums stay near double precision;
+// kComp = false is the plain FP32 sum.
+template <bool kComp>
+struct Acc {
+  float hi, lo;
+  __device__ __forceinline__ void zero() { hi = 0.f; lo = 0.f; }
+  __device__ __forceinline__ void add(float x) {
+    if (kComp) {
+      float s, e;
+      two_sum(hi, x, s, e);
+      hi = s;
+      lo += e;
+    } else {
+      hi += x;
+    }
+  }
+  __device__ __forceinline__ float val() const { return kComp ? hi + lo : hi; }
+};
+
+// -------------------------------------------------------- kernel params
+struct RayDiag {
+  float exit_pos[3];
+  float tau;
+  float ln_s;
+  int steps;
+  int status;
+};
+
+enum RayStatus { kExitOuter = 1, kHitInner = 2, kTauStop = 3, kStepLimit = 4, kMiss = 5, kNan = 6 };
+
+struct TraceParams {
+  GridDev G;
+  float h, h2_6, h_6, h2_12, hrsun;  // step and derived constants, hrsun = h R_sun [cm]
+  float eta, eps_fixed;              // eps = eta |dr|, or eps_fixed when > 0
+  float tau_stop;                    // <= 0: never
+  int max_steps;
+  int tbc_mode;
+  float tbc_K;
+  int emission;
+  int straight;
+  // view
+  float ox, oy, oz, eux, euy, euz, evx, evy, evz;
+  float x0, dx, y0, dy;
+  int nx, ny, npix;
+  int nf;
+  FreqDev freq[kMaxFreq];
+  float* tb_out;
+  RayDiag* diag;
+  unsigned int* counter;            // work queue ticket (zeroed before launch)
+  unsigned long long* stats;        // [0] ray steps, [1] rays
+  unsigned int total;               // nf * npix work items
+};
+
+}  // namespace rt

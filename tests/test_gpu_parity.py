@@ -1,0 +1,329 @@
+"""GPU parity: librt's CUDA path against the FP64 oracle, element by element
+on the same seeded inputs, through the C ABI.
+
+Bars.
+  strict (well-conditioned rays; the spherically symmetric corona):
+    |dT_b| <= 1e-3 * max(T_b, 1e-2 * max over the map of T_b),
+    exit position <= 1e-4 R_sun for rays ending on a sphere, same status.
+  conditioned (rough coronae): a ray's path on the trilinear interpolant is
+    chaotic where stage points fall within rounding distance of a cell face
+    (the interpolant's gradient jumps there).  The oracle measures each ray's
+    own single-precision conditioning by re-tracing it with r, theta, phi
+    perturbed at the 3e-7 level (two seeds); a ray must then match within
+    max(strict bar, 4 x its spread), and rays whose spread stays below a
+    tenth of the strict bar must meet the strict bar, status included.
+"""
+import numpy as np
+import pytest
+
+import corona_synth as cs
+
+pytestmark = pytest.mark.gpu
+
+TB_REL = 1e-3
+EXIT_ABS = 1e-4
+JITTER = 3e-7
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_02413_gb300 import build
+    build.build()
+    import paper_2606_02413_gb300 as rt
+    return rt
+
+
+@pytest.fixture(scope="module")
+def ctx(rt):
+    return rt.Context(0)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return cs.tiny_workload()
+
+
+def smooth_grid():
+    """The tiny grid with a smooth, non-symmetric modulation of n_e and T_e."""
+    g, _, _ = cs.tiny_workload()
+    R, T, P = np.meshgrid(g.r, g.theta, g.phi, indexing="ij")
+    return cs.Grid(g.r, g.theta, g.phi, g.ne * (1 + 0.3 * np.sin(2 * T) * np.cos(P - 0.5) * np.exp(-(R - 1))),
+                   g.te * (1 + 0.2 * np.cos(T) * np.sin(2 * P)))
+
+
+def run_gpu(rt, ctx, grid_obj, v, freqs, **opt):
+    import torch
+    tb, d = ctx.trace_image(grid_obj, v, freqs, rt.options(**opt), diag=True)
+    torch.cuda.synchronize()
+    nf = len(np.atleast_1d(freqs))
+    dd = rt.diag_to_numpy(d)
+    out = {"tb": tb.cpu().numpy().reshape(nf, -1).astype(np.float64)}
+    for k, a in dd.items():
+        out[k] = a.reshape((nf, -1) + a.shape[3:])
+    return out
+
+
+def run_oracle(orc, g, v, freqs, pixels=None, **opt):
+    opt.setdefault("tau_stop", 30.0)
+    opt.pop("precision", None)
+    return orc.trace(orc.grid_field(g), v, freqs, orc.default_options(**opt), pixels=pixels)
+
+
+def spreads(orc, g, v, freqs, ref, pixels=None, **opt):
+    """Per-ray single-precision conditioning of the oracle (T_b, exit, status flips)."""
+    stb = np.zeros_like(ref["tb"])
+    sex = np.zeros(ref["tb"].shape)
+    flip = np.zeros(ref["tb"].shape, bool)
+    for seed in (1, 2):
+        j = run_oracle(orc, g, v, freqs, pixels=pixels, jitter=JITTER, jitter_seed=seed, **dict(opt))
+        stb = np.maximum(stb, np.abs(j["tb"] - ref["tb"]))
+        sex = np.maximum(sex, np.linalg.norm(j["exit"] - ref["exit"], axis=-1))
+        flip |= j["status"] != ref["status"]
+    return stb, sex, flip
+
+
+def _scale(ref_tb):
+    return np.maximum(ref_tb, np.maximum(1e-2 * ref_tb.max(axis=1, keepdims=True), 1e-30))
+
+
+def compare(gpu, ref, pixels=None, tb_rel=TB_REL, exit_abs=EXIT_ABS, lns_abs=None, cond=None, label=""):
+    sel = (lambda a: a) if pixels is None else (lambda a: a[:, pixels])
+    g_tb, g_st, g_ex, g_ls = sel(gpu["tb"]), sel(gpu["status"]), sel(gpu["exit"]), sel(gpu["ln_s"])
+    scale = _scale(ref["tb"])
+    dtb = np.abs(g_tb - ref["tb"])
+    dex = np.linalg.norm(g_ex - ref["exit"], axis=-1)
+    ends = (ref["status"] == 1) | (ref["status"] == 2)
+    if cond is None:
+        well = np.ones(ref["tb"].shape, bool)
+        tb_bound = tb_rel * scale
+        ex_bound = np.full(dex.shape, exit_abs)
+    else:
+        stb, sex, flip = cond
+        well = (stb <= 0.1 * tb_rel * scale) & (sex <= 0.1 * exit_abs) & ~flip
+        tb_bound = np.maximum(tb_rel * scale, 4 * stb)
+        ex_bound = np.maximum(exit_abs, 4 * sex)
+        assert well.mean() >= 0.5, f"{label}: only {well.mean():.0%} of rays well-conditioned"
+    bad_st = well & (g_st != ref["status"])
+    assert not bad_st.any(), f"{label}: status differs at {np.argwhere(bad_st)[:5]}"
+    bad_tb = dtb > tb_bound
+    assert not bad_tb.any(), (f"{label}: T_b out of bounds at {np.argwhere(bad_tb)[:5]}, "
+                              f"max rel {(dtb / scale).max():.3e}")
+    chk = ends & well & (g_st == ref["status"])
+    if chk.any():
+        bad_ex = chk & (dex > ex_bound)
+        assert not bad_ex.any(), f"{label}: exit error {dex[chk].max():.3e} R_sun"
+    if lns_abs is not None:
+        dl = np.abs(g_ls - ref["ln_s"])[well]
+        assert dl.max() <= lns_abs, f"{label}: ln S error {dl.max():.3e}"
+    return {"max_tb_rel": float((dtb / scale).max()), "max_exit": float(dex[ends].max()) if ends.any() else 0.0,
+            "well": float(well.mean())}
+
+
+# ------------------------------------------------------------ field row
+
+def test_field_probe_matches_oracle(rt, ctx, orc):
+    """Field evaluation (trilinear n_e, T_e and the exact gradient) at random
+    points, including the polar caps, the phi wrap, below r_min and in the
+    outer vacuum band, against the oracle's interpolant."""
+    import torch
+    g = smooth_grid()
+    grid = ctx.load(g)
+    F = orc.grid_field(g)
+    rng = np.random.default_rng(4)
+    pts = rng.normal(size=(4000, 3))
+    pts *= (rng.uniform(0.95, 4.0, size=(4000, 1)) / np.linalg.norm(pts, axis=1, keepdims=True))
+    pts[:200, :2] *= 1e-3                          # near the poles
+    pts[200:400, 1] = np.abs(pts[200:400, 1]) * 1e-4  # just across phi = 0
+    pts = pts.astype(np.float32).astype(np.float64)
+    out = ctx.probe_field(grid, pts).cpu().numpy().astype(np.float64)
+    torch.cuda.synchronize()
+    n_bad = 0
+    for p, o in zip(pts, out):
+        ne, gr, te = orc.field_eval(F, p)
+        assert abs(o[0] - ne) <= 2e-6 * abs(ne) + 1e-3, (p, o[0], ne)
+        assert abs(o[1] - te) <= 2e-6 * abs(te) + 1e-3, (p, o[1], te)
+        gn = np.linalg.norm(gr)
+        if np.linalg.norm(o[2:] - gr) > 1e-4 * gn + 1e-6:
+            n_bad += 1  # a point within rounding of a cell face takes the neighbour cell's gradient
+    assert n_bad <= 4, n_bad
+
+
+# ------------------------------------------------------------ strict parity
+
+def test_tiny_full_map_mixed(rt, ctx, orc, tiny):
+    """64x64 map of the spherically symmetric corona at 100 MHz, 4 neighbours,
+    compensated form: the strict bar on every ray, ln S to 1e-4."""
+    g, v, f = tiny
+    grid = ctx.load(g)
+    gpu = run_gpu(rt, ctx, grid, v, f, precision=1)
+    ref = run_oracle(orc, g, v, f)
+    compare(gpu, ref, lns_abs=1e-4, label="tiny mixed")
+    assert (np.abs(gpu["steps"] - ref["steps"]) <= 1).all()
+    st = ctx.stats()
+    assert st["rays"] == 64 * 64 and st["ray_steps"] == int(gpu["steps"].sum())
+
+
+def test_tiny_full_map_plain(rt, ctx, orc, tiny):
+    """Plain FP32 (uncompensated sums): meets the T_b bar; its exit points and
+    ln S drift by the accumulated rounding of ~3000 steps (bounded here at
+    1e-3 R_sun and 1e-2), which the compensated form removes."""
+    g, v, f = tiny
+    grid = ctx.load(g)
+    gpu = run_gpu(rt, ctx, grid, v, f, precision=0)
+    ref = run_oracle(orc, g, v, f)
+    compare(gpu, ref, exit_abs=1e-3, lns_abs=1e-2, label="tiny plain")
+
+
+@pytest.mark.parametrize("freq", [40e6, 250e6, 800e6])
+def test_tiny_other_frequencies(rt, ctx, orc, tiny, freq):
+    g, _, _ = tiny
+    v = cs.View(0.0, 0.0, 31, 29, -2.5, 2.5, -2.4, 2.6)  # ragged sizes
+    grid = ctx.load(g)
+    gpu = run_gpu(rt, ctx, grid, v, [freq], precision=1)
+    ref = run_oracle(orc, g, v, [freq])
+    compare(gpu, ref, lns_abs=1e-4, label=f"tiny {freq / 1e6:.0f} MHz")
+
+
+@pytest.mark.parametrize("n_nb,s_mode", [(2, 0), (4, 0), (8, 0), (4, 2)])
+def test_neighbour_counts_and_modes(rt, ctx, orc, n_nb, s_mode):
+    """2 (paper), 4 and 8 neighbours and magnification off, on a smooth
+    non-symmetric corona seen from an off-axis observer."""
+    g = smooth_grid()
+    v = cs.View(0.7, 0.3, 13, 7, -2.2, 2.6, -1.9, 2.1)
+    freqs = [45e6, 150e6, 700e6]
+    grid = ctx.load(g)
+    gpu = run_gpu(rt, ctx, grid, v, freqs, n_nb=n_nb, s_mode=s_mode, precision=1)
+    ref = run_oracle(orc, g, v, freqs, n_nb=n_nb, s_mode=s_mode)
+    cond = spreads(orc, g, v, freqs, ref, n_nb=n_nb, s_mode=s_mode)
+    compare(gpu, ref, cond=cond, lns_abs=1e-3 if s_mode == 0 else 0.0, label=f"nb{n_nb} mode{s_mode}")
+
+
+def test_rough_corona_conditioned(rt, ctx, orc, tiny):
+    """White-noise modulation at the cell scale (the worst case for the
+    interpolant's face kinks): matched within each ray's conditioning."""
+    g, _, _ = tiny
+    rng = np.random.default_rng(3)
+    gm = cs.Grid(g.r, g.theta, g.phi, g.ne * (1 + 0.3 * rng.random(g.ne.shape)),
+                 g.te * (1 + 0.2 * rng.random(g.ne.shape)))
+    v = cs.View(0.7, 0.3, 13, 7, -2.2, 2.6, -1.9, 2.1)
+    freqs = [45e6, 150e6]
+    grid = ctx.load(gm)
+    gpu = run_gpu(rt, ctx, grid, v, freqs, precision=1)
+    ref = run_oracle(orc, gm, v, freqs)
+    compare(gpu, ref, cond=spreads(orc, gm, v, freqs, ref), label="rough")
+
+
+def test_straight_line_of_sight(rt, ctx, orc, tiny):
+    g = smooth_grid()
+    v = cs.View(0.3, -0.2, 9, 9, -2.0, 2.0, -2.0, 2.0)
+    grid = ctx.load(g)
+    gpu = run_gpu(rt, ctx, grid, v, [80e6, 400e6], straight=1, precision=1)
+    ref = run_oracle(orc, g, v, [80e6, 400e6], straight=1, s_mode=2)
+    compare(gpu, ref, label="LOS")
+
+
+def test_options_edge_cases(rt, ctx, orc, tiny):
+    g, _, _ = tiny
+    v = cs.View(0.0, 0.0, 6, 5, -4.5, 4.5, -4.5, 4.5)  # corners miss the r_max sphere
+    grid = ctx.load(g)
+    for opt in (dict(emission=0, tbc_mode=1, tbc_K=1e4), dict(tau_stop=3.0), dict(max_steps=25),
+                dict(eps_mode=1, delta=5e-4), dict(dtau=4e-3), dict(tbc_mode=1, tbc_K=2e5)):
+        gpu = run_gpu(rt, ctx, grid, v, [120e6, 400e6], precision=1, **opt)
+        ref = run_oracle(orc, g, v, [120e6, 400e6], **dict(opt))
+        compare(gpu, ref, label=str(opt))
+    assert np.any(ref["status"] == 5)
+
+
+def test_single_pixel_and_max_frequencies(rt, ctx, orc, tiny):
+    g, _, _ = tiny
+    grid = ctx.load(g)
+    v1 = cs.View(0.2, 0.0, 1, 1, 0.3, 0.5, -0.2, 0.0)
+    freqs = cs.log_freqs(64, 40e6, 800e6)
+    gpu = run_gpu(rt, ctx, grid, v1, freqs, precision=1)
+    ref = run_oracle(orc, g, v1, freqs)
+    compare(gpu, ref, label="1 pixel x 64 f")
+
+
+def test_deterministic_and_both_forms_agree(rt, ctx, tiny):
+    import torch
+    g, v, f = tiny
+    grid = ctx.load(g)
+    a = ctx.trace_image(grid, v, [60e6, 200e6], rt.options(precision=0))
+    b = ctx.trace_image(grid, v, [60e6, 200e6], rt.options(precision=0))
+    c = ctx.trace_image(grid, v, [60e6, 200e6], rt.options(precision=1))
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert (a - c).abs().max().item() <= 1e-3 * c.abs().max().item()
+
+
+def test_invalid_arguments(rt, ctx, tiny):
+    g, v, f = tiny
+    grid = ctx.load(g)
+    with pytest.raises(rt.RtError, match="RT_ERR_ARG"):
+        ctx.trace_image(grid, v, [], rt.options())
+    with pytest.raises(rt.RtError, match="RT_ERR_ARG"):
+        ctx.trace_image(grid, v, np.full(65, 1e8), rt.options())
+    with pytest.raises(rt.RtError, match="RT_ERR_ARG"):
+        ctx.trace_image(grid, v, [-1.0], rt.options())
+    for bad in (dict(dtau=0.0), dict(n_nb=3), dict(precision=7), dict(s_mode=9)):
+        with pytest.raises(rt.RtError, match="RT_ERR_ARG"):
+            ctx.trace_image(grid, v, [1e8], rt.options(**bad))
+    ne = g.ne.copy()
+    ne[3, 4, 5] = np.nan
+    with pytest.raises(rt.RtError, match="RT_ERR_GRID"):
+        ctx.load_grid(g.r, g.theta, g.phi, ne, g.te)
+    ne = g.ne.copy()
+    ne[1, 1, 1] = -1.0
+    with pytest.raises(rt.RtError, match="RT_ERR_GRID"):
+        ctx.load_grid(g.r, g.theta, g.phi, ne, g.te)
+    te = g.te.copy()
+    te[0, 0, 0] = 0.0
+    with pytest.raises(rt.RtError, match="RT_ERR_GRID"):
+        ctx.load_grid(g.r, g.theta, g.phi, g.ne, te)
+    r = g.r.copy()
+    r[5] = r[4]
+    with pytest.raises(rt.RtError, match="RT_ERR_GRID"):
+        ctx.load_grid(r, g.theta, g.phi, g.ne, g.te)
+    th = g.theta.copy()
+    th[3] += 1e-3
+    with pytest.raises(rt.RtError, match="RT_ERR_GRID"):
+        ctx.load_grid(g.r, th, g.phi, g.ne, g.te)
+    # the context still works afterwards
+    tb = ctx.trace_image(grid, cs.View(0, 0, 2, 2), [1e8], rt.options())
+    ctx.sync()
+    assert np.isfinite(tb.cpu().numpy()).all()
+
+
+def test_device_resident_grid_input(rt, ctx, orc, tiny):
+    import torch
+    g, _, _ = tiny
+    v = cs.View(0.0, 0.0, 8, 8, -2.5, 2.5, -2.5, 2.5)
+    grid = ctx.load_grid(g.r, g.theta, g.phi, torch.from_numpy(g.ne).cuda(), torch.from_numpy(g.te).cuda())
+    gpu = run_gpu(rt, ctx, grid, v, [100e6], precision=1)
+    ref = run_oracle(orc, g, v, [100e6])
+    compare(gpu, ref, label="device grid")
+
+
+def sample_pixels(nx, ny, n, seed=0):
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(nx * ny, size=n, replace=False)).astype(np.int32)
+
+
+def test_global_corona_sampled(rt, ctx, orc):
+    """The 256x180x360 MAS-like corona, 512x512 x 16 frequencies, in the
+    launch configuration the benchmark times; 48 sampled pixels at every
+    frequency against the oracle, within each ray's conditioning."""
+    g, v, f = cs.global_workload()
+    grid = ctx.load(g)
+    gpu = run_gpu(rt, ctx, grid, v, f, precision=1)
+    pix = sample_pixels(v.nx, v.ny, 48, seed=1)
+    ref = run_oracle(orc, g, v, f, pixels=pix)
+    cond = spreads(orc, g, v, f, ref, pixels=pix)
+    res = compare(gpu, ref, pixels=pix, cond=cond, label="global mixed")
+    print("global parity", res)
+    # invariants at full size: every ray finished with a terminal status
+    assert np.isin(gpu["status"], [1, 2, 3, 5]).all()
+    assert np.isfinite(gpu["tb"]).all() and (gpu["tb"] >= 0).all()
