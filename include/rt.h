@@ -165,6 +165,41 @@ rt_status rt_trace_image(rt_ctx* ctx, const rt_grid* grid, const rt_view* view,
                          const double* freqs_hz, int nf, const rt_options* opt,
                          float* tb_out, rt_ray_diag* diag, void* stream);
 
+/* One image request of a batch: a view and its frequencies. */
+typedef struct {
+  const rt_view* view;     /* host                                                */
+  const double* freqs_hz;  /* host, nf entries, each > 0                          */
+  int nf;                  /* >= 1                                                */
+  float* tb_out;           /* device [nf][ny][nx] float, caller-owned             */
+  rt_ray_diag* diag;       /* device [nf][ny][nx] or NULL                         */
+} rt_request;
+
+typedef struct rt_batch_plan rt_batch_plan;
+
+/* Plans one launch over heterogeneous requests (many images, frequencies
+ * and observer longitudes at once; the per-ray work is that of
+ * rt_trace_image, Sec. 3.2).  The rays are cut into chunks of up to 64
+ * pixels of one (request, frequency) map and ordered longest-first by a
+ * path-length estimate (entry chord, and the turning radius where the
+ * shell-mean plasma frequency equals f); one persistent kernel takes them
+ * from a device ticket queue, so rays of very uneven length keep every warp
+ * busy.  The plan owns its device tables and a few bytes of scratch (the
+ * queue ticket and counters) and captures {reset scratch, kernel} in a CUDA
+ * graph.  Synchronous (uploads the tables).  The requests' output buffers
+ * must stay valid while the plan is launched.  Errors: RT_ERR_ARG,
+ * RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_batch_plan_create(rt_ctx* ctx, const rt_grid* grid, const rt_request* reqs, int nreq,
+                               const rt_options* opt, rt_batch_plan** out);
+/* Replays the plan's graph on `stream` (asynchronous). */
+rt_status rt_batch_plan_launch(rt_batch_plan* plan, void* stream);
+/* Counters of the plan's most recent launch (waits for `stream`). */
+rt_status rt_batch_plan_stats(rt_batch_plan* plan, void* stream, rt_stats* out);
+rt_status rt_batch_plan_destroy(rt_batch_plan* plan);
+
+/* One-shot batch: plan, launch on `stream`, wait for it, release the plan. */
+rt_status rt_trace_batch(rt_ctx* ctx, const rt_grid* grid, const rt_request* reqs, int nreq,
+                         const rt_options* opt, void* stream);
+
 /* Samples the interpolated corona at n points: the field evaluation of
  * every RK4 stage (trilinear n_e, T_e in (r, theta, phi) and the exact
  * Cartesian gradient of the n_e interpolant; Sec. 3.1-3.2, Eq. 4).

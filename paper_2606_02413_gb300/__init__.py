@@ -18,7 +18,7 @@ from . import _abi
 from ._abi import (RT_MAG_OFF, RT_MIXED, RT_PLAIN_F32, RT_STEPWISE, RT_TUBE, RAY_STATUS, RtError,
                    check, lib)
 
-__all__ = ["Context", "Grid", "options", "view", "RtError", "RT_STEPWISE", "RT_TUBE", "RT_MAG_OFF",
+__all__ = ["Context", "Grid", "BatchPlan", "options", "view", "RtError", "RT_STEPWISE", "RT_TUBE", "RT_MAG_OFF",
            "RT_PLAIN_F32", "RT_MIXED", "RAY_STATUS", "diag_to_numpy"]
 
 
@@ -64,6 +64,54 @@ class Grid:
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+class BatchPlan:
+    """rt_batch_plan: one graph-captured persistent launch over many requests.
+    ``outputs`` holds each request's T_b tensor [nf, ny, nx] (and diag)."""
+
+    def __init__(self, ctx: "Context", grid: Grid, requests, opts=None, diag=False):
+        import torch
+        self.ctx = ctx
+        self._keep = []
+        n = len(requests)
+        arr = (_abi.Request * n)()
+        self.outputs = []
+        dev = torch.device("cuda", ctx.device)
+        for i, req in enumerate(requests):
+            v = view(req.view)
+            f = np.ascontiguousarray(np.atleast_1d(req.freqs_hz), dtype=np.float64)
+            tb = torch.empty((len(f), v.ny, v.nx), dtype=torch.float32, device=dev)
+            d = torch.empty((len(f), v.ny, v.nx, 7), dtype=torch.int32, device=dev) if diag else None
+            self._keep += [v, f]
+            arr[i] = _abi.Request(C.pointer(v), f.ctypes.data_as(C.POINTER(C.c_double)), len(f), tb.data_ptr(),
+                                  d.data_ptr() if d is not None else None)
+            self.outputs.append((tb, d) if diag else tb)
+        self._arr = arr
+        o = opts if opts is not None else options()
+        h = C.c_void_p()
+        check(lib().rt_batch_plan_create(ctx.handle, grid.handle, arr, n, C.byref(o), C.byref(h)),
+              "rt_batch_plan_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        check(lib().rt_batch_plan_launch(self.handle, _stream_ptr(stream)), "rt_batch_plan_launch")
+
+    def stats(self, stream=None):
+        s = _abi.Stats()
+        check(lib().rt_batch_plan_stats(self.handle, _stream_ptr(stream), C.byref(s)), "rt_batch_plan_stats")
+        return {"ray_steps": int(s.ray_steps), "rays": int(s.rays)}
+
+    def destroy(self):
+        if self.handle:
+            lib().rt_batch_plan_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
         except Exception:
             pass
 
@@ -142,6 +190,10 @@ class Context:
                                    C.c_void_p(out.data_ptr()), C.c_void_p(d.data_ptr() if d is not None else 0),
                                    _stream_ptr(stream)), "rt_trace_image")
         return (out, d) if diag else out
+
+    def batch_plan(self, grid: Grid, requests, opts=None, diag=False) -> BatchPlan:
+        """rt_batch_plan_create over requests (objects with .view and .freqs_hz)."""
+        return BatchPlan(self, grid, requests, opts, diag)
 
     def probe_field(self, grid: Grid, xyz, stream=None):
         """rt_probe_field: (n_e, T_e, grad n_e) at points xyz [n, 3] -> [n, 5]."""

@@ -22,7 +22,9 @@ RAY_STATUS = {1: "EXIT_OUTER", 2: "HIT_INNER", 3: "TAU_STOP", 4: "STEP_LIMIT", 5
 
 # every symbol include/rt.h declares
 EXPORTS = ["rt_default_options", "rt_status_string", "rt_last_error", "rt_create", "rt_destroy",
-           "rt_load_grid", "rt_free_grid", "rt_trace_image", "rt_probe_field", "rt_sync", "rt_get_stats"]
+           "rt_load_grid", "rt_free_grid", "rt_trace_image", "rt_batch_plan_create", "rt_batch_plan_launch",
+           "rt_batch_plan_stats", "rt_batch_plan_destroy", "rt_trace_batch", "rt_probe_field", "rt_sync",
+           "rt_get_stats"]
 
 
 class GridDesc(C.Structure):
@@ -46,6 +48,11 @@ class Options(C.Structure):
 class RayDiag(C.Structure):
     _fields_ = [("exit_pos", C.c_float * 3), ("tau", C.c_float), ("ln_s", C.c_float),
                 ("steps", C.c_int32), ("status", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("view", C.POINTER(View)), ("freqs_hz", C.POINTER(C.c_double)), ("nf", C.c_int),
+                ("tb_out", C.c_void_p), ("diag", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -85,10 +92,16 @@ def lib():
         L.rt_trace_image.argtypes = [vp, vp, C.POINTER(View), C.POINTER(C.c_double), ip,
                                      C.POINTER(Options), vp, vp, vp]
         L.rt_probe_field.argtypes = [vp, vp, vp, ip, vp, vp]
+        L.rt_batch_plan_create.argtypes = [vp, vp, C.POINTER(Request), ip, C.POINTER(Options), C.POINTER(vp)]
+        L.rt_batch_plan_launch.argtypes = [vp, vp]
+        L.rt_batch_plan_stats.argtypes = [vp, vp, C.POINTER(Stats)]
+        L.rt_batch_plan_destroy.argtypes = [vp]
+        L.rt_trace_batch.argtypes = [vp, vp, C.POINTER(Request), ip, C.POINTER(Options), vp]
         L.rt_sync.argtypes = [vp, vp]
         L.rt_get_stats.argtypes = [vp, vp, C.POINTER(Stats)]
         for name in ("rt_create", "rt_destroy", "rt_load_grid", "rt_free_grid", "rt_trace_image",
-                     "rt_probe_field", "rt_sync", "rt_get_stats"):
+                     "rt_batch_plan_create", "rt_batch_plan_launch", "rt_batch_plan_stats",
+                     "rt_batch_plan_destroy", "rt_trace_batch", "rt_probe_field", "rt_sync", "rt_get_stats"):
             getattr(L, name).restype = ip
         _lib = L
         return _lib

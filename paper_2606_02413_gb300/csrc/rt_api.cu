@@ -70,6 +70,20 @@ struct rt_grid {
   int2* lut = nullptr;
   float2* rcell = nullptr;
   int n_r = 0, n_t = 0, n_p = 0;
+  std::vector<double> r;         // radial nodes
+  std::vector<double> shell_ne;  // mean n_e over each r shell (work estimates)
+};
+
+struct rt_batch_plan {
+  rt_ctx* ctx = nullptr;
+  ChunkDev* chunks = nullptr;
+  MapDev* maps = nullptr;
+  ViewDev* views = nullptr;
+  unsigned int* counter = nullptr;
+  unsigned long long* stats = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
 };
 
 // --------------------------------------------------------------- kernels
@@ -100,6 +114,22 @@ __global__ void pack_cells(const T* __restrict__ ne, const T* __restrict__ te, f
   }
 }
 
+// Mean n_e over each radial shell (one block per shell).
+template <class T>
+__global__ void shell_mean(const T* __restrict__ ne, int n_tp, double* out) {
+  __shared__ double part[256];
+  double acc = 0.0;
+  const T* row = ne + (long)blockIdx.x * n_tp;
+  for (int i = threadIdx.x; i < n_tp; i += blockDim.x) acc += (double)row[i];
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = part[0] / n_tp;
+}
+
 // Flags non-finite or negative n_e and non-finite or non-positive T_e.
 template <class T>
 __global__ void check_values(const T* __restrict__ ne, const T* __restrict__ te, long n, unsigned int* bad) {
@@ -115,7 +145,7 @@ __global__ void check_values(const T* __restrict__ ne, const T* __restrict__ te,
 __global__ void probe_field(const GridDev G, const float* __restrict__ xyz, int n, float* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const Sample s = eval_field<true>(G, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]);
+  const Sample s = eval_field(G, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], true);
   out[5 * i] = s.ne;
   out[5 * i + 1] = s.te;
   out[5 * i + 2] = s.gx;
@@ -290,12 +320,16 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
   void* tmp_te = nullptr;
   unsigned int* d_bad = nullptr;
   unsigned int h_bad = 0;
+  double* d_shell = nullptr;
+  g->shell_ne.assign(nr, 0.0);
+  g->r.assign(R, R + nr);
   auto cleanup = [&](bool keep) {
     if (d->on_device == 0) {
       cudaFree(tmp_ne);
       cudaFree(tmp_te);
     }
     cudaFree(d_bad);
+    cudaFree(d_shell);
     if (!keep) {
       cudaFree(g->ne); cudaFree(g->te); cudaFree(g->lut); cudaFree(g->rcell);
       delete g;
@@ -307,6 +341,7 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
   if (e == cudaSuccess) e = cudaMalloc(&g->lut, sizeof(int2) * nb);
   if (e == cudaSuccess) e = cudaMalloc(&g->rcell, sizeof(float2) * (nr - 1));
   if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&d_shell, sizeof(double) * nr);
   if (e == cudaSuccess && d->on_device == 0) {
     e = cudaMalloc(&tmp_ne, esz * nodes);
     if (e == cudaSuccess) e = cudaMalloc(&tmp_te, esz * nodes);
@@ -331,13 +366,17 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
     if (d->dtype == RT_F64) {
       check_values<double><<<blocks, 256, 0, s>>>((const double*)src_ne, (const double*)src_te, nodes, d_bad);
       pack_cells<double><<<blocks, 256, 0, s>>>((const double*)src_ne, (const double*)src_te, g->ne, g->te, nr, nt, np);
+      shell_mean<double><<<nr, 256, 0, s>>>((const double*)src_ne, nt * np, d_shell);
     } else {
       check_values<float><<<blocks, 256, 0, s>>>((const float*)src_ne, (const float*)src_te, nodes, d_bad);
       pack_cells<float><<<blocks, 256, 0, s>>>((const float*)src_ne, (const float*)src_te, g->ne, g->te, nr, nt, np);
+      shell_mean<float><<<nr, 256, 0, s>>>((const float*)src_ne, nt * np, d_shell);
     }
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, d_bad, sizeof h_bad, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->shell_ne.data(), d_shell, sizeof(double) * nr, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     cleanup(false);
@@ -408,22 +447,35 @@ static rt_status check_view(const rt_view* v) {
   return RT_OK;
 }
 
-rt_status rt_trace_image(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const double* freqs, int nf,
-                         const rt_options* o, float* tb_out, rt_ray_diag* diag, void* stream) {
-  if (!ctx || !g || !freqs || !tb_out) return fail(RT_ERR_ARG, "rt_trace_image: NULL argument");
-  rt_status st = check_view(v);
-  if (st != RT_OK) return st;
-  int nb = 0;
-  st = check_options(o, &nb);
-  if (st != RT_OK) return st;
-  if (nf < 1 || nf > kMaxFreq) return fail(RT_ERR_ARG, "rt_trace_image: nf = %d (1..%d)", nf, kMaxFreq);
-  for (int i = 0; i < nf; ++i)
-    if (!(freqs[i] > 0.0) || !std::isfinite(freqs[i])) return fail(RT_ERR_ARG, "frequency %d is not > 0", i);
-  const long total = (long)nf * v->nx * v->ny;
-  if (total >= (1L << 31)) return fail(RT_ERR_ARG, "rt_trace_image: too many rays");
+}  // extern "C"
 
-  TraceParams P;
-  std::memset(&P, 0, sizeof P);
+namespace {
+
+ViewDev make_view(const rt_view& v) {
+  ViewDev V;
+  const double cl = std::cos(v.lon_rad), sl = std::sin(v.lon_rad), cb = std::cos(v.lat_rad), sb = std::sin(v.lat_rad);
+  V.ox = (float)(cb * cl); V.oy = (float)(cb * sl); V.oz = (float)sb;
+  V.eux = (float)(-sl); V.euy = (float)cl; V.euz = 0.f;
+  V.evx = (float)(-sb * cl); V.evy = (float)(-sb * sl); V.evz = (float)cb;
+  V.x0 = (float)v.x0; V.dx = (float)((v.x1 - v.x0) / v.nx);
+  V.y0 = (float)v.y0; V.dy = (float)((v.y1 - v.y0) / v.ny);
+  V.nx = v.nx;
+  V.npix = v.nx * v.ny;
+  return V;
+}
+
+FreqDev make_freq(double f, int slab) {
+  const double cpe = c_pe();
+  FreqDev F;
+  F.kf = (float)(-cpe / (2.0 * f * f));
+  F.kn2 = (float)(-cpe / (f * f));
+  F.kap_c = (float)(9.78e-3 / (f * f));
+  F.ln_f = (float)std::log(f);
+  F.out_slab = slab;
+  return F;
+}
+
+void fill_common(TraceParams& P, const rt_grid* g, const rt_options* o) {
   P.G = g->dev;
   const double h = o->dtau;
   P.h = (float)h;
@@ -439,27 +491,57 @@ rt_status rt_trace_image(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const 
   P.tbc_K = (float)o->tbc_K;
   P.emission = o->emission;
   P.straight = o->straight;
-  const double cl = std::cos(v->lon_rad), sl = std::sin(v->lon_rad), cb = std::cos(v->lat_rad), sb = std::sin(v->lat_rad);
-  P.ox = (float)(cb * cl); P.oy = (float)(cb * sl); P.oz = (float)sb;
-  P.eux = (float)(-sl); P.euy = (float)cl; P.euz = 0.f;
-  P.evx = (float)(-sb * cl); P.evy = (float)(-sb * sl); P.evz = (float)cb;
-  P.x0 = (float)v->x0; P.dx = (float)((v->x1 - v->x0) / v->nx);
-  P.y0 = (float)v->y0; P.dy = (float)((v->y1 - v->y0) / v->ny);
-  P.nx = v->nx; P.ny = v->ny; P.npix = v->nx * v->ny;
+}
+
+bool bad_freq(double f) { return !(f > 0.0) || !std::isfinite(f); }
+
+// Estimated RK4 steps of a ray with impact parameter b (in units of h):
+// the entry chord, cut at the turning radius r_c where the shell-mean
+// plasma frequency equals f, or at the inner sphere.
+double path_estimate(double b, double rc, double rmin, double rmax) {
+  if (b >= rmax) return 1.0;
+  const double out = std::sqrt(rmax * rmax - b * b);
+  const double stop = std::max(rc, rmin);
+  if (b >= stop) return 2.0 * out;
+  const double in = std::sqrt(stop * stop - b * b);
+  return (rc > rmin) ? 2.0 * (out - in) : out - in;
+}
+
+double turning_radius(const rt_grid* g, double f) {
+  const double nc = f * f / c_pe();
+  for (int i = g->n_r - 1; i >= 0; --i)
+    if (g->shell_ne[i] >= nc) return g->r[i];
+  return 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+rt_status rt_trace_image(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const double* freqs, int nf,
+                         const rt_options* o, float* tb_out, rt_ray_diag* diag, void* stream) {
+  if (!ctx || !g || !freqs || !tb_out) return fail(RT_ERR_ARG, "rt_trace_image: NULL argument");
+  rt_status st = check_view(v);
+  if (st != RT_OK) return st;
+  int nb = 0;
+  st = check_options(o, &nb);
+  if (st != RT_OK) return st;
+  if (nf < 1 || nf > kMaxFreq) return fail(RT_ERR_ARG, "rt_trace_image: nf = %d (1..%d)", nf, kMaxFreq);
+  for (int i = 0; i < nf; ++i)
+    if (bad_freq(freqs[i])) return fail(RT_ERR_ARG, "frequency %d is not > 0", i);
+  const long total = (long)nf * v->nx * v->ny;
+  if (total >= (1L << 31)) return fail(RT_ERR_ARG, "rt_trace_image: too many rays");
+
+  TraceParams P;
+  std::memset(&P, 0, sizeof P);
+  fill_common(P, g, o);
+  P.view = make_view(*v);
   P.nf = nf;
   // lowest frequencies first: their rays turn high and tend to be longest
   std::vector<int> order(nf);
   for (int i = 0; i < nf; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return freqs[a] < freqs[b]; });
-  const double cpe = c_pe();
-  for (int i = 0; i < nf; ++i) {
-    const double f = freqs[order[i]];
-    P.freq[i].kf = (float)(-cpe / (2.0 * f * f));
-    P.freq[i].kn2 = (float)(-cpe / (f * f));
-    P.freq[i].kap_c = (float)(9.78e-3 / (f * f));
-    P.freq[i].ln_f = (float)std::log(f);
-    P.freq[i].out_slab = order[i];
-  }
+  for (int i = 0; i < nf; ++i) P.freq[i] = make_freq(freqs[order[i]], order[i]);
   P.tb_out = tb_out;
   P.diag = reinterpret_cast<RayDiag*>(diag);
   P.counter = ctx->d_counter;
@@ -471,6 +553,140 @@ rt_status rt_trace_image(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const 
   RT_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), s));
   RT_CUDA(cudaMemsetAsync(ctx->d_stats, 0, 2 * sizeof(unsigned long long), s));
   RT_CUDA(dispatch_trace(nb, o->precision == RT_MIXED, P, ctx->sm_count, s));
+  return RT_OK;
+}
+
+rt_status rt_batch_plan_destroy(rt_batch_plan* p) {
+  if (!p) return fail(RT_ERR_ARG, "rt_batch_plan_destroy: NULL plan");
+  if (p->ctx) cudaSetDevice(p->ctx->device);
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->cap) cudaStreamDestroy(p->cap);
+  cudaFree(p->chunks);
+  cudaFree(p->maps);
+  cudaFree(p->views);
+  cudaFree(p->counter);
+  cudaFree(p->stats);
+  delete p;
+  return RT_OK;
+}
+
+rt_status rt_batch_plan_create(rt_ctx* ctx, const rt_grid* g, const rt_request* reqs, int nreq,
+                               const rt_options* o, rt_batch_plan** out) {
+  if (!ctx || !g || !reqs || !out) return fail(RT_ERR_ARG, "rt_batch_plan_create: NULL argument");
+  *out = nullptr;
+  if (nreq < 1) return fail(RT_ERR_ARG, "rt_batch_plan_create: nreq = %d", nreq);
+  int nb = 0;
+  rt_status st = check_options(o, &nb);
+  if (st != RT_OK) return st;
+  std::vector<ViewDev> views;
+  std::vector<MapDev> maps;
+  struct Cand { double cost; ChunkDev c; };
+  std::vector<Cand> cands;
+  const double rmin = g->r.front(), rmax = g->r.back();
+  for (int q = 0; q < nreq; ++q) {
+    const rt_request& R = reqs[q];
+    if (!R.view || !R.freqs_hz || !R.tb_out || R.nf < 1) return fail(RT_ERR_ARG, "request %d: NULL field or nf < 1", q);
+    st = check_view(R.view);
+    if (st != RT_OK) return st;
+    views.push_back(make_view(*R.view));
+    const int npix = R.view->nx * R.view->ny;
+    const double du = (R.view->x1 - R.view->x0) / R.view->nx, dv = (R.view->y1 - R.view->y0) / R.view->ny;
+    for (int fi = 0; fi < R.nf; ++fi) {
+      if (bad_freq(R.freqs_hz[fi])) return fail(RT_ERR_ARG, "request %d frequency %d is not > 0", q, fi);
+      MapDev M;
+      M.f = make_freq(R.freqs_hz[fi], fi);
+      M.view = q;
+      M.out = R.tb_out + (size_t)fi * npix;
+      M.diag = R.diag ? reinterpret_cast<RayDiag*>(R.diag) + (size_t)fi * npix : nullptr;
+      const int m = (int)maps.size();
+      maps.push_back(M);
+      const double rc = turning_radius(g, R.freqs_hz[fi]);
+      for (int p0 = 0; p0 < npix; p0 += kChunk) {
+        const int cnt = std::min(kChunk, npix - p0);
+        double cost = 0.0;
+        for (int k = 0; k < cnt; k += 8) {
+          const int pix = p0 + k, ix = pix % R.view->nx, iy = pix / R.view->nx;
+          const double u = R.view->x0 + (ix + 0.5) * du, v = R.view->y0 + (iy + 0.5) * dv;
+          cost += path_estimate(std::sqrt(u * u + v * v), rc, rmin, rmax);
+        }
+        cands.push_back({cost, ChunkDev{m, p0, cnt, 0}});
+      }
+    }
+  }
+  if ((double)cands.size() * kChunk >= 4.0e9) return fail(RT_ERR_ARG, "rt_batch_plan_create: too many rays");
+  std::stable_sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) { return a.cost > b.cost; });
+  std::vector<ChunkDev> chunks(cands.size());
+  for (size_t i = 0; i < cands.size(); ++i) chunks[i] = cands[i].c;
+
+  RT_CUDA(cudaSetDevice(ctx->device));
+  rt_batch_plan* p = new rt_batch_plan;
+  p->ctx = ctx;
+  cudaError_t e = cudaMalloc(&p->chunks, sizeof(ChunkDev) * chunks.size());
+  if (e == cudaSuccess) e = cudaMalloc(&p->maps, sizeof(MapDev) * maps.size());
+  if (e == cudaSuccess) e = cudaMalloc(&p->views, sizeof(ViewDev) * views.size());
+  if (e == cudaSuccess) e = cudaMalloc(&p->counter, 64);
+  if (e == cudaSuccess) e = cudaMalloc(&p->stats, 64);
+  if (e == cudaSuccess) e = cudaMemcpy(p->chunks, chunks.data(), sizeof(ChunkDev) * chunks.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->maps, maps.data(), sizeof(MapDev) * maps.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->views, views.data(), sizeof(ViewDev) * views.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+  TraceParams P;
+  std::memset(&P, 0, sizeof P);
+  fill_common(P, g, o);
+  P.chunks = p->chunks;
+  P.maps = p->maps;
+  P.views = p->views;
+  P.counter = p->counter;
+  P.stats = p->stats;
+  P.total = (unsigned int)(chunks.size() * kChunk);
+  // capture {reset ticket and counters, persistent kernel} once; replay per launch
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = cudaMemsetAsync(p->counter, 0, sizeof(unsigned int), p->cap);
+    cudaError_t e2 = cudaMemsetAsync(p->stats, 0, 2 * sizeof(unsigned long long), p->cap);
+    cudaError_t e3 = dispatch_trace(nb, o->precision == RT_MIXED, P, ctx->sm_count, p->cap);
+    e = cudaStreamEndCapture(p->cap, &p->graph);
+    if (e == cudaSuccess) e = (e1 != cudaSuccess) ? e1 : (e2 != cudaSuccess) ? e2 : e3;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+  if (e != cudaSuccess) {
+    rt_batch_plan_destroy(p);
+    return fail(e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "rt_batch_plan_create: %s",
+                cudaGetErrorString(e));
+  }
+  *out = p;
+  return RT_OK;
+}
+
+rt_status rt_batch_plan_launch(rt_batch_plan* p, void* stream) {
+  if (!p) return fail(RT_ERR_ARG, "rt_batch_plan_launch: NULL plan");
+  RT_CUDA(cudaSetDevice(p->ctx->device));
+  RT_CUDA(cudaGraphLaunch(p->exec, (cudaStream_t)stream));
+  return RT_OK;
+}
+
+rt_status rt_batch_plan_stats(rt_batch_plan* p, void* stream, rt_stats* out) {
+  if (!p || !out) return fail(RT_ERR_ARG, "rt_batch_plan_stats: NULL argument");
+  RT_CUDA(cudaSetDevice(p->ctx->device));
+  unsigned long long h[2] = {0, 0};
+  RT_CUDA(cudaMemcpyAsync(h, p->stats, sizeof h, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  RT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  out->ray_steps = h[0];
+  out->rays = h[1];
+  return RT_OK;
+}
+
+rt_status rt_trace_batch(rt_ctx* ctx, const rt_grid* g, const rt_request* reqs, int nreq, const rt_options* o,
+                         void* stream) {
+  rt_batch_plan* p = nullptr;
+  rt_status st = rt_batch_plan_create(ctx, g, reqs, nreq, o, &p);
+  if (st != RT_OK) return st;
+  st = rt_batch_plan_launch(p, stream);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  rt_batch_plan_destroy(p);
+  if (st != RT_OK) return st;
+  if (e != cudaSuccess) return fail(RT_ERR_CUDA, "rt_trace_batch: %s", cudaGetErrorString(e));
   return RT_OK;
 }
 

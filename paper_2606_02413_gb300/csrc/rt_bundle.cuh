@@ -71,55 +71,71 @@ __device__ __forceinline__ float chord_crossing(const Vec& r, const Vec& dr, flo
   return fminf(a, 1.f);
 }
 
+// Per-bundle state of the central lane, kept in shared memory so that only
+// the RK4 state lives in registers across the four field evaluations.
+struct BundleState {
+  float* out;                                           // T_b of this ray
+  RayDiag* dg;                                          // its diagnostics or null
+  int step, status;
+  float kf, kap_c, ln_f;                                // frequency constants
+  float tau_hi, tau_lo, lns_hi, lns_lo, tb_hi, tb_lo;  // running sums (lo: compensation)
+  float rl[3], kl[3];                                   // compensation of r and k
+  float kap_prev, te_prev;                              // node i-1 transfer values
+  float t[3], e1[3], e2[3], eps;                        // basis of the retraced step
+  float g0[3];                                          // central G of that step (2 neighbours)
+  float alpha, pc[3];                                   // clipped last step
+  unsigned long long steps_done, rays_done;
+};
+
+template <bool kComp>
+__device__ __forceinline__ void acc_add(float& hi, float& lo, float x) {
+  if (kComp) {
+    float s, e;
+    two_sum(hi, x, s, e);
+    hi = s;
+    lo += e;
+  } else {
+    hi += x;
+  }
+}
+
 template <int NB, bool kMixed>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __grid_constant__ TraceParams P) {
   constexpr int L = NB + 1;
   constexpr int BPW = 32 / L;
+  __shared__ BundleState S[kThreads / 32][BPW];
   const int lane = threadIdx.x & 31;
   const int q = lane % L;
   const bool used = (lane / L) < BPW;
   const int base = used ? lane - q : lane;
   const bool central = used && q == 0;
+  BundleState& B = S[threadIdx.x >> 5][used ? lane / L : 0];
   const float h = P.h;
 
-  // ---- per-lane RK4 start state
+  if (central) {
+    B.steps_done = 0;
+    B.rays_done = 0;
+  }
+  // ---- per-lane RK4 start state (central: its node; neighbour: its seed)
   float px = 0.f, py = 0.f, pz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
   bool has_seed = false;  // neighbour lanes: a retrace is pending
-  // ---- central-lane bundle state
-  int phase = 0;          // 0 needs work, 1 stepping, 2 final (clipped) segment
-  bool exhausted = !used || !central;
-  unsigned int item = 0;
-  int fi = 0, pix = 0;
-  float kf = 0.f;
-  int step = 0;
-  Acc<kMixed> tau, lns, tb;
-  tau.zero(); lns.zero(); tb.zero();
-  float rlx = 0.f, rly = 0.f, rlz = 0.f, klx = 0.f, kly = 0.f, klz = 0.f;  // compensation terms
-  float kap_prev = 0.f, te_prev = 0.f;
-  Vec tp{0.f, 0.f, 1.f}, e1p{1.f, 0.f, 0.f}, e2p{0.f, 1.f, 0.f};  // basis of the step being retraced
-  float epsp = 1.f;
-  Vec g0p{0.f, 0.f, 0.f};  // central G of that step (one-sided 2-neighbour form)
-  bool emitted = false;    // neighbours retrace a step in this iteration
-  float alpha = 1.f;
-  Vec pc{0.f, 0.f, 0.f};
-  int status = 0;
-  unsigned long long my_steps = 0, my_rays = 0;
+  int phase = 0;          // central: 0 needs work, 1 stepping, 2 final (clipped) segment
+  bool emitted = false;   // central: its neighbours retrace a step this iteration
+  bool exhausted = !central;
 
-  auto finish = [&](int st, const Vec& endp, float tb_val) {
-    const FreqDev& F = P.freq[fi];
-    const size_t o = (size_t)F.out_slab * P.npix + pix;
-    P.tb_out[o] = tb_val;
-    if (P.diag) {
+  auto finish = [&](int st, float ex, float ey, float ez, float tb_val) {
+    *B.out = tb_val;
+    if (B.dg) {
       RayDiag d;
-      d.exit_pos[0] = endp.x; d.exit_pos[1] = endp.y; d.exit_pos[2] = endp.z;
-      d.tau = tau.val();
-      d.ln_s = lns.val();
-      d.steps = step;
+      d.exit_pos[0] = ex; d.exit_pos[1] = ey; d.exit_pos[2] = ez;
+      d.tau = B.tau_hi + B.tau_lo;
+      d.ln_s = B.lns_hi + B.lns_lo;
+      d.steps = B.step;
       d.status = st;
-      P.diag[o] = d;
+      *B.dg = d;
     }
-    my_steps += (unsigned long long)step;
-    my_rays += 1;
+    B.steps_done += (unsigned long long)B.step;
+    B.rays_done += 1;
     phase = 0;
   };
 
@@ -133,46 +149,72 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
       if (lane == leader) first = atomicAdd(P.counter, (unsigned)__popc(needmask));
       first = __shfl_sync(kFull, first, leader);
       if (need) {
-        item = first + __popc(needmask & ((1u << lane) - 1u));
+        const unsigned int item = first + __popc(needmask & ((1u << lane) - 1u));
         if (item >= P.total) {
           exhausted = true;
           need = false;
         } else {
-          // launch (Sec. 3.2): entry point on the outer sphere, k = n(r0) (-o)
-          fi = item / P.npix;
-          pix = item - fi * P.npix;
-          const FreqDev& F = P.freq[fi];
-          kf = P.straight ? 0.f : F.kf;
-          const int ix = pix % P.nx, iy = pix / P.nx;
-          const float u = fmaf((float)ix + 0.5f, P.dx, P.x0);
-          const float v = fmaf((float)iy + 0.5f, P.dy, P.y0);
-          const float R = P.G.r_max;
-          const float b2 = fmaf(u, u, v * v);
-          step = 0;
-          tau.zero(); lns.zero(); tb.zero();
-          rlx = rly = rlz = klx = kly = klz = 0.f;
-          emitted = false;
-          bool ok = b2 < R * R;
-          float nn = 1.f;
-          Vec r0{0.f, 0.f, 0.f};
-          if (ok) {
-            const float s = sqrtf(fmaf(R, R, -b2));
-            r0 = {fmaf(u, P.eux, fmaf(v, P.evx, s * P.ox)), fmaf(u, P.euy, fmaf(v, P.evy, s * P.oy)),
-                  fmaf(u, P.euz, fmaf(v, P.evz, s * P.oz))};
-            if (!P.straight) {
-              const Sample s0 = eval_field<false>(P.G, r0.x, r0.y, r0.z);
-              const float n2 = fmaf(F.kn2, s0.ne, 1.f);
-              ok = n2 > 0.f;
-              nn = ok ? sqrtf(n2) : 0.f;
-            }
-          }
-          if (!ok) {
-            finish(kMiss, r0, 0.f);
+          // decode the ticket into (view, frequency, pixel, output)
+          const ViewDev* V;
+          const FreqDev* F;
+          int pix;
+          bool valid = true;
+          if (P.chunks) {
+            const ChunkDev c = P.chunks[item >> kChunkShift];
+            const int off = (int)(item & (kChunk - 1));
+            valid = off < c.count;
+            const MapDev& M = P.maps[c.map];
+            pix = c.pix0 + off;
+            V = &P.views[M.view];
+            F = &M.f;
+            B.out = M.out + pix;
+            B.dg = M.diag ? M.diag + pix : nullptr;
           } else {
-            px = r0.x; py = r0.y; pz = r0.z;
-            kx = -nn * P.ox; ky = -nn * P.oy; kz = -nn * P.oz;
-            phase = 1;
-            need = false;
+            const int fi = item / P.view.npix;
+            pix = item - fi * P.view.npix;
+            V = &P.view;
+            F = &P.freq[fi];
+            const size_t o = (size_t)F->out_slab * P.view.npix + pix;
+            B.out = P.tb_out + o;
+            B.dg = P.diag ? P.diag + o : nullptr;
+          }
+          if (valid) {  // a ragged chunk tail has no ray behind the ticket: take another
+            // launch (Sec. 3.2): entry point on the outer sphere, k = n(r0) (-o)
+            B.kf = P.straight ? 0.f : F->kf;
+            B.kap_c = F->kap_c;
+            B.ln_f = F->ln_f;
+            B.step = 0;
+            B.tau_hi = B.tau_lo = B.lns_hi = B.lns_lo = B.tb_hi = B.tb_lo = 0.f;
+            B.rl[0] = B.rl[1] = B.rl[2] = B.kl[0] = B.kl[1] = B.kl[2] = 0.f;
+            emitted = false;
+            const int ix = pix % V->nx, iy = pix / V->nx;
+            const float u = fmaf((float)ix + 0.5f, V->dx, V->x0);
+            const float v = fmaf((float)iy + 0.5f, V->dy, V->y0);
+            const float R = P.G.r_max;
+            const float b2 = fmaf(u, u, v * v);
+            bool ok = b2 < R * R;
+            float nn = 1.f;
+            float r0x = 0.f, r0y = 0.f, r0z = 0.f;
+            if (ok) {
+              const float s = sqrtf(fmaf(R, R, -b2));
+              r0x = fmaf(u, V->eux, fmaf(v, V->evx, s * V->ox));
+              r0y = fmaf(u, V->euy, fmaf(v, V->evy, s * V->oy));
+              r0z = fmaf(u, V->euz, fmaf(v, V->evz, s * V->oz));
+              if (!P.straight) {
+                const Sample s0 = eval_field(P.G, r0x, r0y, r0z, false);
+                const float n2 = fmaf(F->kn2, s0.ne, 1.f);
+                ok = n2 > 0.f;
+                nn = ok ? sqrtf(n2) : 0.f;
+              }
+            }
+            if (!ok) {
+              finish(kMiss, r0x, r0y, r0z, 0.f);
+            } else {
+              px = r0x; py = r0y; pz = r0z;
+              kx = -nn * V->ox; ky = -nn * V->oy; kz = -nn * V->oz;
+              phase = 1;
+              need = false;
+            }
           }
         }
       }
@@ -182,43 +224,34 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
 
     // ------------------------------------------------------------ RK4
     // central lanes step (phase 1); neighbour lanes retrace (has_seed)
+    const float kf_lane = __shfl_sync(kFull, (central && phase != 0) ? B.kf : 0.f, base);
     const bool work = central ? (phase == 1) : has_seed;
     Rk4Out o;
     o.Gx = o.Gy = o.Gz = o.Ax = o.Ay = o.Az = 0.f;
     o.ne1 = o.te1 = 0.f;
-    const float kf_lane = __shfl_sync(kFull, kf, base);
     if (work) o = rk4_step(P.G, kf_lane, h, px, py, pz, kx, ky, kz, central);
     if (central && phase == 2) {  // the clip point closes the path
-      const Sample s = eval_field<true>(P.G, pc.x, pc.y, pc.z);
+      const Sample s = eval_field(P.G, B.pc[0], B.pc[1], B.pc[2], true);
       o.ne1 = s.ne;
       o.te1 = s.te;
     }
 
     // ------------------------------------------------- neighbour exchange
-    Vec c1{0.f, 0.f, 0.f}, c2{0.f, 0.f, 0.f}, c3{0.f, 0.f, 0.f}, c4{0.f, 0.f, 0.f};
+    // raw separations: NB >= 4: D_j = G_{+j} - G_{-j}; NB == 2: G_j
+    Vec d1{0.f, 0.f, 0.f}, d2{0.f, 0.f, 0.f}, d3{0.f, 0.f, 0.f}, d4{0.f, 0.f, 0.f};
     if (NB == 2) {
-      const float gx1 = __shfl_sync(kFull, o.Gx, base + 1), gy1 = __shfl_sync(kFull, o.Gy, base + 1),
-                  gz1 = __shfl_sync(kFull, o.Gz, base + 1);
-      const float gx2 = __shfl_sync(kFull, o.Gx, base + 2), gy2 = __shfl_sync(kFull, o.Gy, base + 2),
-                  gz2 = __shfl_sync(kFull, o.Gz, base + 2);
-      const float s = P.h2_6 / epsp;  // one-sided: d_j = eps e_j + h^2/6 (G_j - G_0)
-      c1 = {s * (gx1 - g0p.x), s * (gy1 - g0p.y), s * (gz1 - g0p.z)};
-      c2 = {s * (gx2 - g0p.x), s * (gy2 - g0p.y), s * (gz2 - g0p.z)};
+      d1 = {__shfl_sync(kFull, o.Gx, base + 1), __shfl_sync(kFull, o.Gy, base + 1), __shfl_sync(kFull, o.Gz, base + 1)};
+      d2 = {__shfl_sync(kFull, o.Gx, base + 2), __shfl_sync(kFull, o.Gy, base + 2), __shfl_sync(kFull, o.Gz, base + 2)};
     } else if (NB >= 4) {
       // "+" members (odd roles) form G_+ - G_- with their "-" partner
       const float dx = o.Gx - __shfl_down_sync(kFull, o.Gx, 1);
       const float dy = o.Gy - __shfl_down_sync(kFull, o.Gy, 1);
       const float dz = o.Gz - __shfl_down_sync(kFull, o.Gz, 1);
-      const float s = P.h2_12 / epsp;  // central difference: d = eps e + h^2/12 (G_+ - G_-)
-      c1 = {s * __shfl_sync(kFull, dx, base + 1), s * __shfl_sync(kFull, dy, base + 1),
-            s * __shfl_sync(kFull, dz, base + 1)};
-      c2 = {s * __shfl_sync(kFull, dx, base + 3), s * __shfl_sync(kFull, dy, base + 3),
-            s * __shfl_sync(kFull, dz, base + 3)};
+      d1 = {__shfl_sync(kFull, dx, base + 1), __shfl_sync(kFull, dy, base + 1), __shfl_sync(kFull, dz, base + 1)};
+      d2 = {__shfl_sync(kFull, dx, base + 3), __shfl_sync(kFull, dy, base + 3), __shfl_sync(kFull, dz, base + 3)};
       if (NB == 8) {
-        c3 = {s * __shfl_sync(kFull, dx, base + 5), s * __shfl_sync(kFull, dy, base + 5),
-              s * __shfl_sync(kFull, dz, base + 5)};
-        c4 = {s * __shfl_sync(kFull, dx, base + 7), s * __shfl_sync(kFull, dy, base + 7),
-              s * __shfl_sync(kFull, dz, base + 7)};
+        d3 = {__shfl_sync(kFull, dx, base + 5), __shfl_sync(kFull, dy, base + 5), __shfl_sync(kFull, dz, base + 5)};
+        d4 = {__shfl_sync(kFull, dx, base + 7), __shfl_sync(kFull, dy, base + 7), __shfl_sync(kFull, dz, base + 7)};
       }
     }
 
@@ -226,67 +259,87 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
     bool emit = false;
     Vec sr{0.f, 0.f, 0.f}, sk{0.f, 0.f, 0.f}, sa{0.f, 0.f, 0.f}, sb{0.f, 0.f, 0.f};
     if (central && phase != 0) {
-      const FreqDev& F = P.freq[fi];
       if (emitted && NB > 0) {  // M of the step the neighbours just retraced (Eqs. 9-11)
+        const Vec tp{B.t[0], B.t[1], B.t[2]};
+        const Vec e1p{B.e1[0], B.e1[1], B.e1[2]}, e2p{B.e2[0], B.e2[1], B.e2[2]};
+        Vec c1, c2;
+        if (NB == 2) {  // one-sided: d_j = eps e_j + h^2/6 (G_j - G_0)
+          const float sc = P.h2_6 / B.eps;
+          c1 = {sc * (d1.x - B.g0[0]), sc * (d1.y - B.g0[1]), sc * (d1.z - B.g0[2])};
+          c2 = {sc * (d2.x - B.g0[0]), sc * (d2.y - B.g0[1]), sc * (d2.z - B.g0[2])};
+        } else {        // central difference: d = eps e + h^2/12 (G_+ - G_-)
+          const float sc = P.h2_12 / B.eps;
+          c1 = {sc * d1.x, sc * d1.y, sc * d1.z};
+          c2 = {sc * d2.x, sc * d2.y, sc * d2.z};
+        }
         float lm = ln_m(c1, c2, e1p, e2p, tp);
         if (NB == 8) {
-          const float s2 = 0.70710678118654752f;
+          const float s2 = 0.70710678118654752f, sc = P.h2_12 / B.eps;
           const Vec g1{s2 * (e1p.x + e2p.x), s2 * (e1p.y + e2p.y), s2 * (e1p.z + e2p.z)};
           const Vec g2{s2 * (e2p.x - e1p.x), s2 * (e2p.y - e1p.y), s2 * (e2p.z - e1p.z)};
+          const Vec c3{sc * d3.x, sc * d3.y, sc * d3.z}, c4{sc * d4.x, sc * d4.y, sc * d4.z};
           const float lm2 = ln_m(c3, c4, g1, g2, tp);
           // M = (M_e + M_g) / 2
           lm = fmaxf(lm, lm2) + log1p_small(__expf(-fabsf(lm - lm2))) - 0.69314718055994531f;
         }
-        lns.add(lm);
+        acc_add<kMixed>(B.lns_hi, B.lns_lo, lm);
       }
-      const float kap = P.emission ? kappa_vac(o.ne1, o.te1, F) : 0.f;
+      const float kap = P.emission ? kappa_vac(o.ne1, o.te1, B.kap_c, B.ln_f) : 0.f;
       bool done = false;
       if (phase == 2) {
         // clipped last segment + boundary term (Eq. 2 front to back)
-        const float dt = 0.5f * (kap_prev + kap) * P.hrsun * alpha;
-        const float tbar = 0.5f * (te_prev + o.te1);
-        tb.add(tbar * one_minus_exp_neg(dt) * __expf(lns.val() - tau.val()));
-        tau.add(dt);
+        const float dt = 0.5f * (B.kap_prev + kap) * P.hrsun * B.alpha;
+        const float tbar = 0.5f * (B.te_prev + o.te1);
+        const float lns = B.lns_hi + B.lns_lo;
+        acc_add<kMixed>(B.tb_hi, B.tb_lo, tbar * one_minus_exp_neg(dt) * __expf(lns - (B.tau_hi + B.tau_lo)));
+        acc_add<kMixed>(B.tau_hi, B.tau_lo, dt);
         float tbc = 0.f;
-        if (status == kHitInner) tbc = (P.tbc_mode == 1) ? P.tbc_K : o.te1;
-        if (tbc != 0.f) tb.add(tbc * __expf(lns.val() - tau.val()));
-        step += 1;
-        finish(status, pc, tb.val());
+        if (B.status == kHitInner) tbc = (P.tbc_mode == 1) ? P.tbc_K : o.te1;
+        if (tbc != 0.f) acc_add<kMixed>(B.tb_hi, B.tb_lo, tbc * __expf(lns - (B.tau_hi + B.tau_lo)));
+        B.step += 1;
+        finish(B.status, B.pc[0], B.pc[1], B.pc[2], B.tb_hi + B.tb_lo);
         done = true;
       } else {
+        const int step = B.step;
         if (step >= 1) {
           // segment step-1 -> step (Eq. 2 with Eq. 12, front to back)
-          const float dt = 0.5f * (kap_prev + kap) * P.hrsun;
-          const float tbar = 0.5f * (te_prev + o.te1);
-          tb.add(tbar * one_minus_exp_neg(dt) * __expf(lns.val() - tau.val()));
-          tau.add(dt);
-          const Vec here{px, py, pz};
-          if (P.tau_stop > 0.f && tau.val() >= P.tau_stop) {
-            finish(kTauStop, here, tb.val());
+          const float dt = 0.5f * (B.kap_prev + kap) * P.hrsun;
+          const float tbar = 0.5f * (B.te_prev + o.te1);
+          const float tau0 = B.tau_hi + B.tau_lo;
+          acc_add<kMixed>(B.tb_hi, B.tb_lo, tbar * one_minus_exp_neg(dt) * __expf((B.lns_hi + B.lns_lo) - tau0));
+          acc_add<kMixed>(B.tau_hi, B.tau_lo, dt);
+          if (P.tau_stop > 0.f && B.tau_hi + B.tau_lo >= P.tau_stop) {
+            finish(kTauStop, px, py, pz, B.tb_hi + B.tb_lo);
             done = true;
           } else if (step >= P.max_steps) {
-            finish(kStepLimit, here, tb.val());
+            finish(kStepLimit, px, py, pz, B.tb_hi + B.tb_lo);
             done = true;
           }
         }
         if (!done) {
           // complete central step `step` (Eq. 4, RK4 increment form)
-          const float kxx = kx + klx, kyy = ky + kly, kzz = kz + klz;
-          const Vec dr{fmaf(h, kxx, P.h2_6 * o.Gx), fmaf(h, kyy, P.h2_6 * o.Gy), fmaf(h, kzz, P.h2_6 * o.Gz)};
+          float rlx = B.rl[0], rly = B.rl[1], rlz = B.rl[2];
+          float klx = B.kl[0], kly = B.kl[1], klz = B.kl[2];
+          const Vec dr{fmaf(h, kx + klx, P.h2_6 * o.Gx), fmaf(h, ky + kly, P.h2_6 * o.Gy),
+                       fmaf(h, kz + klz, P.h2_6 * o.Gz)};
           const Vec dk{P.h_6 * o.Ax, P.h_6 * o.Ay, P.h_6 * o.Az};
           sr = {px, py, pz};
           sk = {kx, ky, kz};
           // chord, basis and eps of this step (Eqs. 5, 6, 8)
-          const float d2 = dot3(dr, dr);
-          const float ids = rsqrtf(d2);
-          const float ds = d2 * ids;
-          tp = {dr.x * ids, dr.y * ids, dr.z * ids};
+          const float d2n = dot3(dr, dr);
+          const float ids = rsqrtf(d2n);
+          const Vec tp{dr.x * ids, dr.y * ids, dr.z * ids};
           if (NB > 0) {
+            Vec e1p, e2p;
             basis(tp, e1p, e2p);
-            epsp = (P.eps_fixed > 0.f) ? P.eps_fixed : P.eta * ds;
-            sa = {epsp * e1p.x, epsp * e1p.y, epsp * e1p.z};
-            sb = {epsp * e2p.x, epsp * e2p.y, epsp * e2p.z};
-            g0p = {o.Gx, o.Gy, o.Gz};
+            const float eps = (P.eps_fixed > 0.f) ? P.eps_fixed : P.eta * (d2n * ids);
+            B.t[0] = tp.x; B.t[1] = tp.y; B.t[2] = tp.z;
+            B.e1[0] = e1p.x; B.e1[1] = e1p.y; B.e1[2] = e1p.z;
+            B.e2[0] = e2p.x; B.e2[1] = e2p.y; B.e2[2] = e2p.z;
+            B.eps = eps;
+            sa = {eps * e1p.x, eps * e1p.y, eps * e1p.z};
+            sb = {eps * e2p.x, eps * e2p.y, eps * e2p.z};
+            if (NB == 2) { B.g0[0] = o.Gx; B.g0[1] = o.Gy; B.g0[2] = o.Gz; }
             emit = true;
           }
           Vec rn, kn;
@@ -298,32 +351,36 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
             two_sum(kx, dk.x + klx, kn.x, e); klx = e;
             two_sum(ky, dk.y + kly, kn.y, e); kly = e;
             two_sum(kz, dk.z + klz, kn.z, e); klz = e;
+            B.rl[0] = rlx; B.rl[1] = rly; B.rl[2] = rlz;
+            B.kl[0] = klx; B.kl[1] = kly; B.kl[2] = klz;
           } else {
             rn = {px + dr.x, py + dr.y, pz + dr.z};
             kn = {kx + dk.x, ky + dk.y, kz + dk.z};
           }
-          const Vec here{px, py, pz};
           const float rr2 = dot3(rn, rn);
-          kap_prev = kap;
-          te_prev = o.te1;
+          B.kap_prev = kap;
+          B.te_prev = o.te1;
+          const Vec here{px, py, pz};
           if (rr2 < P.G.r_min * P.G.r_min) {
-            status = kHitInner;
-            alpha = chord_crossing(here, dr, P.G.r_min, false);
-            pc = {fmaf(alpha, dr.x, px), fmaf(alpha, dr.y, py), fmaf(alpha, dr.z, pz)};
+            B.status = kHitInner;
+            const float a = chord_crossing(here, dr, P.G.r_min, false);
+            B.alpha = a;
+            B.pc[0] = fmaf(a, dr.x, px); B.pc[1] = fmaf(a, dr.y, py); B.pc[2] = fmaf(a, dr.z, pz);
             phase = 2;
           } else if (rr2 > P.G.r_max * P.G.r_max && dot3(rn, kn) > 0.f) {
-            status = kExitOuter;
-            alpha = chord_crossing(here, dr, P.G.r_max, true);
-            pc = {fmaf(alpha, dr.x, px), fmaf(alpha, dr.y, py), fmaf(alpha, dr.z, pz)};
+            B.status = kExitOuter;
+            const float a = chord_crossing(here, dr, P.G.r_max, true);
+            B.alpha = a;
+            B.pc[0] = fmaf(a, dr.x, px); B.pc[1] = fmaf(a, dr.y, py); B.pc[2] = fmaf(a, dr.z, pz);
             phase = 2;
           } else if (!isfinite(rr2 + kn.x + kn.y + kn.z)) {
-            step += 1;
-            finish(kNan, rn, tb.val());
+            B.step = step + 1;
+            finish(kNan, rn.x, rn.y, rn.z, B.tb_hi + B.tb_lo);
             emit = false;
           } else {
             px = rn.x; py = rn.y; pz = rn.z;
             kx = kn.x; ky = kn.y; kz = kn.z;
-            step += 1;
+            B.step = step + 1;
           }
         }
       }
@@ -368,6 +425,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
   }
 
   // ---- statistics
+  unsigned long long my_steps = central ? B.steps_done : 0ull, my_rays = central ? B.rays_done : 0ull;
   for (int off = 16; off > 0; off >>= 1) {
     my_steps += __shfl_down_sync(kFull, my_steps, off);
     my_rays += __shfl_down_sync(kFull, my_rays, off);

@@ -63,17 +63,18 @@ __device__ __forceinline__ float atan2_grid(float y, float x) {
 // Trilinear interpolant in (r, theta, phi) (linear in physical r) and its
 // exact gradient chain-ruled to Cartesian:
 //   grad f = f_r r_hat + f_theta theta_hat / r + f_phi phi_hat / (r sin theta).
-template <bool kWantTe>
-__device__ __forceinline__ Sample eval_field(const GridDev& G, float x, float y, float z) {
+// T_e is interpolated with the same weights when want_te (a per-lane flag:
+// only the T_e loads diverge, the evaluation itself stays warp-uniform).
+__device__ __forceinline__ Sample eval_field(const GridDev& G, float x, float y, float z, bool want_te) {
   Sample s;
   const float rho2 = fmaf(x, x, y * y);
   const float r2 = fmaf(z, z, rho2);
-  const float r = sqrtf(r2);
+  const float inv_r = rsqrtf(r2);
+  const float r = r2 * inv_r;
   if (!(r <= G.r_vac)) {  // vacuum beyond the outer band (and NaN positions)
     s.ne = 0.f; s.te = 0.f; s.gx = 0.f; s.gy = 0.f; s.gz = 0.f;
     return s;
   }
-  const float inv_r = __fdividef(1.0f, r);
   // radial cell from the lookup table: at most one node lies inside a bin
   int bin = __float2int_rd((r - G.r_lut0) * G.r_lut_inv);
   bin = min(max(bin, 0), G.r_lut_n - 1);
@@ -82,7 +83,8 @@ __device__ __forceinline__ Sample eval_field(const GridDev& G, float x, float y,
   const float2 rc = __ldg(G.r_cell + i);
   const float u = (r - rc.x) * rc.y;
 
-  const float rho = sqrtf(rho2);
+  const float inv_rho = (rho2 > 0.f) ? rsqrtf(rho2) : 0.f;
+  const float rho = rho2 * inv_rho;
   const float tt = (atan2_grid(rho, z) - G.t0) * G.t_inv;
   int j;
   float v, tsel;
@@ -120,26 +122,21 @@ __device__ __forceinline__ Sample eval_field(const GridDev& G, float x, float y,
   const float f_t = fv * G.t_inv * tsel;
   const float f_p = fw * G.p_inv;
   const float A = f_r * inv_r;
-  float B = 0.f, C = 0.f, D = 0.f;
-  if (rho2 > 0.f) {
-    const float inv_rho = __fdividef(1.0f, rho);
-    const float ir2 = inv_r * inv_r;
-    B = f_t * z * ir2 * inv_rho;  // theta term, x and y components (per x, y)
-    C = f_p * inv_rho * inv_rho;  // phi term
-    D = f_t * rho * ir2;          // theta term, z component
-  }
+  const float ir2 = inv_r * inv_r;
+  const float B = f_t * z * ir2 * inv_rho;   // theta term, x and y components (per x, y)
+  const float C = f_p * inv_rho * inv_rho;   // phi term
+  const float D = f_t * rho * ir2;           // theta term, z component
   s.gx = fmaf(A + B, x, -C * y);
   s.gy = fmaf(A + B, y, C * x);
   s.gz = fmaf(A, z, -D);
-  if (kWantTe) {
+  s.te = 0.f;
+  if (want_te) {
     const float4 t0 = __ldg(G.te + 2 * cell);
     const float4 t1 = __ldg(G.te + 2 * cell + 1);
     const float p00 = fmaf(w, t0.y - t0.x, t0.x), p01 = fmaf(w, t0.w - t0.z, t0.z);
     const float p10 = fmaf(w, t1.y - t1.x, t1.x), p11 = fmaf(w, t1.w - t1.z, t1.z);
     const float q0 = fmaf(v, p01 - p00, p00), q1 = fmaf(v, p11 - p10, p10);
     s.te = fmaf(u, q1 - q0, q0);
-  } else {
-    s.te = 0.f;
   }
   return s;
 }
@@ -160,7 +157,7 @@ __device__ __forceinline__ Rk4Out rk4_step(const GridDev& G, float kf, float h, 
                                            float pz, float kx, float ky, float kz, bool want_te) {
   Rk4Out o;
   const float hh = 0.5f * h;
-  Sample s = want_te ? eval_field<true>(G, px, py, pz) : eval_field<false>(G, px, py, pz);
+  Sample s = eval_field(G, px, py, pz, want_te);
   o.ne1 = s.ne;
   o.te1 = s.te;
   float ax = kf * s.gx, ay = kf * s.gy, az = kf * s.gz;
@@ -168,18 +165,18 @@ __device__ __forceinline__ Rk4Out rk4_step(const GridDev& G, float kf, float h, 
   o.Ax = ax; o.Ay = ay; o.Az = az;
   // stage 2
   float qx = fmaf(hh, ax, kx), qy = fmaf(hh, ay, ky), qz = fmaf(hh, az, kz);
-  s = eval_field<false>(G, fmaf(hh, kx, px), fmaf(hh, ky, py), fmaf(hh, kz, pz));
+  s = eval_field(G, fmaf(hh, kx, px), fmaf(hh, ky, py), fmaf(hh, kz, pz), false);
   ax = kf * s.gx; ay = kf * s.gy; az = kf * s.gz;
   o.Gx += ax; o.Gy += ay; o.Gz += az;
   o.Ax = fmaf(2.f, ax, o.Ax); o.Ay = fmaf(2.f, ay, o.Ay); o.Az = fmaf(2.f, az, o.Az);
   // stage 3
   const float q3x = fmaf(hh, ax, kx), q3y = fmaf(hh, ay, ky), q3z = fmaf(hh, az, kz);
-  s = eval_field<false>(G, fmaf(hh, qx, px), fmaf(hh, qy, py), fmaf(hh, qz, pz));
+  s = eval_field(G, fmaf(hh, qx, px), fmaf(hh, qy, py), fmaf(hh, qz, pz), false);
   ax = kf * s.gx; ay = kf * s.gy; az = kf * s.gz;
   o.Gx += ax; o.Gy += ay; o.Gz += az;
   o.Ax = fmaf(2.f, ax, o.Ax); o.Ay = fmaf(2.f, ay, o.Ay); o.Az = fmaf(2.f, az, o.Az);
   // stage 4
-  s = eval_field<false>(G, fmaf(h, q3x, px), fmaf(h, q3y, py), fmaf(h, q3z, pz));
+  s = eval_field(G, fmaf(h, q3x, px), fmaf(h, q3y, py), fmaf(h, q3z, pz), false);
   o.Ax = fmaf(kf, s.gx, o.Ax); o.Ay = fmaf(kf, s.gy, o.Ay); o.Az = fmaf(kf, s.gz, o.Az);
   return o;
 }
@@ -196,12 +193,12 @@ struct FreqDev {
 // Free-free absorption coefficient in vacuum units [cm^-1] (Dulk 1985,
 // pure hydrogen): 9.78e-3 n_e^2 G / (f^2 T^1.5), G = 24.5 + ln T - ln f
 // (T > 2e5 K) or 18.2 + 1.5 ln T - ln f.
-__device__ __forceinline__ float kappa_vac(float ne, float te, const FreqDev& F) {
+__device__ __forceinline__ float kappa_vac(float ne, float te, float kap_c, float ln_f) {
   if (!(ne > 0.f) || !(te > 0.f)) return 0.f;
   const float lnT = __logf(te);
-  const float g = (te > 2e5f) ? (24.5f + lnT - F.ln_f) : fmaf(1.5f, lnT, 18.2f - F.ln_f);
+  const float g = (te > 2e5f) ? (24.5f + lnT - ln_f) : fmaf(1.5f, lnT, 18.2f - ln_f);
   const float rs = rsqrtf(te);
-  return (F.kap_c * ne) * ne * g * (rs * rs * rs);
+  return (kap_c * ne) * ne * g * (rs * rs * rs);
 }
 
 // 1 - e^-x for x >= 0: Taylor series below 0.05 (truncation < 1e-9
@@ -264,6 +261,32 @@ struct RayDiag {
 
 enum RayStatus { kExitOuter = 1, kHitInner = 2, kTauStop = 3, kStepLimit = 4, kMiss = 5, kNan = 6 };
 
+// Launch geometry of one image (Sec. 3.2): observer direction o, image axes
+// e_u, e_v, and the pixel-centre mapping u = x0 + (ix + 1/2) dx.
+struct ViewDev {
+  float ox, oy, oz, eux, euy, euz, evx, evy, evz;
+  float x0, dx, y0, dy;
+  int nx, npix;
+};
+
+// Batched work: one map = (request, frequency) with its output slab; one
+// chunk = up to kChunk consecutive pixels of one map.  Chunks are listed
+// longest-first; ticket t covers pixel (t mod kChunk) of chunk t / kChunk.
+constexpr int kChunkShift = 6;
+constexpr int kChunk = 1 << kChunkShift;
+struct MapDev {
+  FreqDev f;
+  int view;           // index into the view table
+  float* out;         // [ny][nx] T_b slab of this map
+  RayDiag* diag;      // [ny][nx] or null
+};
+struct ChunkDev {
+  int map;
+  int pix0;           // first pixel of the chunk
+  int count;          // pixels in the chunk (<= kChunk)
+  int pad;
+};
+
 struct TraceParams {
   GridDev G;
   float h, h2_6, h_6, h2_12, hrsun;  // step and derived constants, hrsun = h R_sun [cm]
@@ -274,17 +297,19 @@ struct TraceParams {
   float tbc_K;
   int emission;
   int straight;
-  // view
-  float ox, oy, oz, eux, euy, euz, evx, evy, evz;
-  float x0, dx, y0, dy;
-  int nx, ny, npix;
+  // image mode: one view, nf frequencies, ticket t -> (frequency t / npix, pixel t mod npix)
+  ViewDev view;
   int nf;
   FreqDev freq[kMaxFreq];
   float* tb_out;
   RayDiag* diag;
+  // batch mode (chunks != null): tickets go through the chunk table
+  const ChunkDev* chunks;
+  const MapDev* maps;
+  const ViewDev* views;
   unsigned int* counter;            // work queue ticket (zeroed before launch)
   unsigned long long* stats;        // [0] ray steps, [1] rays
-  unsigned int total;               // nf * npix work items
+  unsigned int total;               // tickets
 };
 
 }  // namespace rt
