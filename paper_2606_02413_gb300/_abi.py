@@ -23,8 +23,8 @@ RAY_STATUS = {1: "EXIT_OUTER", 2: "HIT_INNER", 3: "TAU_STOP", 4: "STEP_LIMIT", 5
 # every symbol include/rt.h declares
 EXPORTS = ["rt_default_options", "rt_status_string", "rt_last_error", "rt_create", "rt_destroy",
            "rt_load_grid", "rt_free_grid", "rt_trace_image", "rt_batch_plan_create", "rt_batch_plan_launch",
-           "rt_batch_plan_stats", "rt_batch_plan_destroy", "rt_trace_batch", "rt_probe_field", "rt_sync",
-           "rt_get_stats"]
+           "rt_batch_plan_stats", "rt_batch_plan_destroy", "rt_trace_batch", "rt_trace_batch_noalloc",
+           "rt_probe_field", "rt_sync", "rt_get_stats"]
 
 
 class GridDesc(C.Structure):
@@ -97,11 +97,13 @@ def lib():
         L.rt_batch_plan_stats.argtypes = [vp, vp, C.POINTER(Stats)]
         L.rt_batch_plan_destroy.argtypes = [vp]
         L.rt_trace_batch.argtypes = [vp, vp, C.POINTER(Request), ip, C.POINTER(Options), vp]
+        L.rt_trace_batch_noalloc.argtypes = [vp, C.POINTER(Request), ip, C.POINTER(Options), vp]
         L.rt_sync.argtypes = [vp, vp]
         L.rt_get_stats.argtypes = [vp, vp, C.POINTER(Stats)]
         for name in ("rt_create", "rt_destroy", "rt_load_grid", "rt_free_grid", "rt_trace_image",
                      "rt_batch_plan_create", "rt_batch_plan_launch", "rt_batch_plan_stats",
-                     "rt_batch_plan_destroy", "rt_trace_batch", "rt_probe_field", "rt_sync", "rt_get_stats"):
+                     "rt_batch_plan_destroy", "rt_trace_batch", "rt_trace_batch_noalloc", "rt_probe_field",
+                     "rt_sync", "rt_get_stats"):
             getattr(L, name).restype = ip
         _lib = L
         return _lib

@@ -720,3 +720,109 @@ rt_status rt_get_stats(rt_ctx* ctx, void* stream, rt_stats* out) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------- allocation-free batch
+// Scratch of rt_trace_batch_noalloc: [0, 256) ticket (u32 at 0) and ray
+// counters (2 x u64 at 8), then the view, map and chunk tables (16-byte
+// aligned).  Host code only ever uses the address returned by
+// cudaGetSymbolAddress for the current device, never the symbol itself.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RT_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+struct NoAllocDevice {
+  std::once_flag once;
+  unsigned char* scratch = nullptr;
+  int sm_count = 0;
+  cudaError_t err = cudaSuccess;
+};
+NoAllocDevice g_noalloc_devices[kMaxDevices];
+
+size_t align16(size_t n) { return (n + 15) & ~size_t(15); }
+
+}  // namespace
+
+extern "C" rt_status rt_trace_batch_noalloc(const rt_grid* g, const rt_request* reqs, int nreq, const rt_options* o,
+                                            void* stream) {
+  if (!g || !reqs) return fail(RT_ERR_ARG, "rt_trace_batch_noalloc: NULL argument");
+  if (nreq < 1) return fail(RT_ERR_ARG, "rt_trace_batch_noalloc: nreq = %d", nreq);
+  int nb = 0;
+  rt_status st = check_options(o, &nb);
+  if (st != RT_OK) return st;
+  int dev = 0;
+  RT_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(RT_ERR_ARG, "rt_trace_batch_noalloc: device %d", dev);
+  NoAllocDevice& D = g_noalloc_devices[dev];
+  std::call_once(D.once, [&D, dev]() {
+    void* p = nullptr;
+    D.err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (D.err == cudaSuccess) D.err = cudaDeviceGetAttribute(&D.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    D.scratch = static_cast<unsigned char*>(p);
+  });
+  if (D.err != cudaSuccess || !D.scratch)
+    return fail(RT_ERR_CUDA, "rt_trace_batch_noalloc: scratch set-up failed: %s", cudaGetErrorString(D.err));
+
+  // tables: one view per request, one map per (request, frequency), chunks
+  // of up to kChunk pixels ordered longest-first
+  std::vector<ViewDev> views;
+  std::vector<MapDev> maps;
+  std::vector<std::pair<double, ChunkDev>> cands;
+  const double rmin = g->r.front(), rmax = g->r.back();
+  for (int q = 0; q < nreq; ++q) {
+    const rt_request& R = reqs[q];
+    if (!R.view || !R.freqs_hz || !R.tb_out || R.nf < 1) return fail(RT_ERR_ARG, "request %d: NULL field or nf < 1", q);
+    st = check_view(R.view);
+    if (st != RT_OK) return st;
+    views.push_back(make_view(*R.view));
+    const int npix = R.view->nx * R.view->ny;
+    const double du = (R.view->x1 - R.view->x0) / R.view->nx, dv = (R.view->y1 - R.view->y0) / R.view->ny;
+    for (int fi = 0; fi < R.nf; ++fi) {
+      if (bad_freq(R.freqs_hz[fi])) return fail(RT_ERR_ARG, "request %d frequency %d is not > 0", q, fi);
+      MapDev M;
+      M.f = make_freq(R.freqs_hz[fi], fi);
+      M.view = q;
+      M.out = R.tb_out + (size_t)fi * npix;
+      M.diag = R.diag ? reinterpret_cast<RayDiag*>(R.diag) + (size_t)fi * npix : nullptr;
+      const int m = (int)maps.size();
+      maps.push_back(M);
+      const double rc = turning_radius(g, R.freqs_hz[fi]);
+      for (int p0 = 0; p0 < npix; p0 += kChunk) {
+        const int pix = p0 + std::min(kChunk, npix - p0) / 2, ix = pix % R.view->nx, iy = pix / R.view->nx;
+        const double u = R.view->x0 + (ix + 0.5) * du, v = R.view->y0 + (iy + 0.5) * dv;
+        cands.push_back({path_estimate(std::sqrt(u * u + v * v), rc, rmin, rmax),
+                         ChunkDev{m, p0, std::min(kChunk, npix - p0), 0}});
+      }
+    }
+  }
+  const size_t off_views = 256;
+  const size_t off_maps = align16(off_views + sizeof(ViewDev) * views.size());
+  const size_t off_chunks = align16(off_maps + sizeof(MapDev) * maps.size());
+  const size_t bytes = off_chunks + sizeof(ChunkDev) * cands.size();
+  if (bytes > RT_NOALLOC_SCRATCH_BYTES)
+    return fail(RT_ERR_ARG, "rt_trace_batch_noalloc: the batch needs %zu bytes of scratch, the static scratch holds %u",
+                bytes, (unsigned)RT_NOALLOC_SCRATCH_BYTES);
+  std::stable_sort(cands.begin(), cands.end(),
+                   [](const std::pair<double, ChunkDev>& a, const std::pair<double, ChunkDev>& b) { return a.first > b.first; });
+  // one host image of the scratch; its zero control block clears the ticket and counters
+  std::vector<unsigned char> img(bytes, 0);
+  std::memcpy(img.data() + off_views, views.data(), sizeof(ViewDev) * views.size());
+  std::memcpy(img.data() + off_maps, maps.data(), sizeof(MapDev) * maps.size());
+  for (size_t i = 0; i < cands.size(); ++i)
+    std::memcpy(img.data() + off_chunks + i * sizeof(ChunkDev), &cands[i].second, sizeof(ChunkDev));
+
+  cudaStream_t s = (cudaStream_t)stream;
+  RT_CUDA(cudaMemcpyAsync(D.scratch, img.data(), bytes, cudaMemcpyHostToDevice, s));
+  TraceParams P;
+  std::memset(&P, 0, sizeof P);
+  fill_common(P, g, o);
+  P.views = reinterpret_cast<const ViewDev*>(D.scratch + off_views);
+  P.maps = reinterpret_cast<const MapDev*>(D.scratch + off_maps);
+  P.chunks = reinterpret_cast<const ChunkDev*>(D.scratch + off_chunks);
+  P.counter = reinterpret_cast<unsigned int*>(D.scratch);
+  P.stats = reinterpret_cast<unsigned long long*>(D.scratch + 8);
+  P.total = (unsigned int)(cands.size() * kChunk);
+  RT_CUDA(dispatch_trace(nb, o->precision == RT_MIXED, P, D.sm_count, s));
+  return RT_OK;
+}
+
