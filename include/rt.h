@@ -200,6 +200,29 @@ rt_status rt_batch_plan_destroy(rt_batch_plan* plan);
 rt_status rt_trace_batch(rt_ctx* ctx, const rt_grid* grid, const rt_request* reqs, int nreq,
                          const rt_options* opt, void* stream);
 
+/* Gradient of a map misfit with respect to the grid (adjoint of
+ * rt_trace_image; the paper's forward method differentiated, Sec. 2.1
+ * Eqs. 4-12 and Sec. 3.2).  For L = sum over pixels and frequencies of
+ * dL_dTb * T_b, returns dL/dn_e and dL/dT_e at every grid node, exact for
+ * the discrete forward computation with its discrete events held fixed
+ * (cell indices, the basis axis branch, the step count, the termination
+ * step).  Internally: the forward pass, a second forward pass that stores
+ * the ray state every 32 central steps, then a reverse sweep that recomputes
+ * each 32-step segment and runs the transfer, tube-area, neighbour-retrace
+ * and RK4 adjoints back through it, scattering node gradients with atomics.
+ * view, freqs_hz, nf, opt: as for rt_trace_image; supported forms: s_mode
+ * RT_STEPWISE with n_nb = 4, or RT_MAG_OFF; not straight lines of sight.
+ * dL_dTb:  device [nf][ny][nx] float.
+ * dL_dne, dL_dte: device [n_r][n_theta][n_phi] float, caller-owned,
+ *          overwritten (zeroed by the call first).
+ * tb_out:  device [nf][ny][nx] float for the forward T_b, or NULL.
+ * Synchronous: returns when the gradients are complete.  Allocates and
+ * frees its own device scratch (checkpoints ~ total ray steps / 32 x 64 B).
+ * Errors: RT_ERR_ARG, RT_ERR_UNSUPPORTED, RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_backward(rt_ctx* ctx, const rt_grid* grid, const rt_view* view, const double* freqs_hz, int nf,
+                      const rt_options* opt, const float* dL_dTb, float* dL_dne, float* dL_dte, float* tb_out,
+                      void* stream);
+
 /* Allocation-free batch.  The paper has no counterpart: this entry point
  * exists for callers that must not allocate device memory when they trace,
  * such as code running while a CUDA stream is being captured into a graph

@@ -18,7 +18,7 @@ from . import _abi
 from ._abi import (RT_MAG_OFF, RT_MIXED, RT_PLAIN_F32, RT_STEPWISE, RT_TUBE, RAY_STATUS, RtError,
                    check, lib)
 
-__all__ = ["Context", "Grid", "BatchPlan", "options", "view", "RtError", "RT_STEPWISE", "RT_TUBE", "RT_MAG_OFF",
+__all__ = ["Context", "Grid", "BatchPlan", "RayTraceFn", "options", "view", "RtError", "RT_STEPWISE", "RT_TUBE", "RT_MAG_OFF",
            "RT_PLAIN_F32", "RT_MIXED", "RAY_STATUS", "diag_to_numpy"]
 
 
@@ -195,6 +195,26 @@ class Context:
         """rt_batch_plan_create over requests (objects with .view and .freqs_hz)."""
         return BatchPlan(self, grid, requests, opts, diag)
 
+    def backward(self, grid: Grid, v, freqs, dL_dTb, opts=None, want_tb=False, stream=None):
+        """rt_backward: gradients of sum(dL_dTb * T_b) w.r.t. the grid node
+        values.  Returns (dL/dn_e, dL/dT_e) as float32 CUDA tensors shaped like
+        the grid (and the forward T_b with want_tb=True)."""
+        import torch
+        vs = view(v)
+        f = np.ascontiguousarray(np.atleast_1d(freqs), dtype=np.float64)
+        dev = torch.device("cuda", self.device)
+        g = torch.as_tensor(dL_dTb, dtype=torch.float32, device=dev).contiguous()
+        assert g.numel() == len(f) * vs.ny * vs.nx
+        dne = torch.empty(grid.shape, dtype=torch.float32, device=dev)
+        dte = torch.empty(grid.shape, dtype=torch.float32, device=dev)
+        tb = torch.empty((len(f), vs.ny, vs.nx), dtype=torch.float32, device=dev) if want_tb else None
+        o = opts if opts is not None else options()
+        check(lib().rt_backward(self.handle, grid.handle, C.byref(vs), f.ctypes.data_as(C.POINTER(C.c_double)),
+                                len(f), C.byref(o), C.c_void_p(g.data_ptr()), C.c_void_p(dne.data_ptr()),
+                                C.c_void_p(dte.data_ptr()), C.c_void_p(tb.data_ptr() if tb is not None else 0),
+                                _stream_ptr(stream)), "rt_backward")
+        return (dne, dte, tb) if want_tb else (dne, dte)
+
     def probe_field(self, grid: Grid, xyz, stream=None):
         """rt_probe_field: (n_e, T_e, grad n_e) at points xyz [n, 3] -> [n, 5]."""
         import torch
@@ -220,3 +240,40 @@ def diag_to_numpy(d):
     return {"exit": f[..., 0:3].astype(np.float64), "tau": f[..., 3].astype(np.float64),
             "ln_s": f[..., 4].astype(np.float64), "steps": a[..., 5].astype(np.int64),
             "status": a[..., 6].astype(np.int32)}
+
+
+class RayTraceFn:
+    """torch.autograd.Function: T_b maps from grid tensors, differentiable
+    with respect to n_e and T_e through rt_backward.
+
+        tb = RayTraceFn.apply(ne, te, ctx, r, theta, phi, view, freqs, opts)
+
+    ne, te: CUDA tensors [n_r, n_theta, n_phi] (float32 or float64)."""
+
+    @staticmethod
+    def _fn():
+        import torch
+
+        class _F(torch.autograd.Function):
+            @staticmethod
+            def forward(fctx, ne, te, ctx, r, theta, phi, v, freqs, opts):
+                grid = ctx.load_grid(r, theta, phi, ne.detach(), te.detach())
+                tb = ctx.trace_image(grid, v, freqs, opts)
+                fctx.state = (ctx, grid, v, freqs, opts, ne.dtype, te.dtype)
+                return tb
+
+            @staticmethod
+            def backward(fctx, grad_tb):
+                ctx, grid, v, freqs, opts, dne_t, dte_t = fctx.state
+                dne, dte = ctx.backward(grid, v, freqs, grad_tb.contiguous(), opts)
+                grid.free()
+                return dne.to(dne_t), dte.to(dte_t), None, None, None, None, None, None, None
+
+        return _F
+
+    @classmethod
+    def apply(cls, *args):
+        if not hasattr(cls, "_impl"):
+            cls._impl = cls._fn()
+        return cls._impl.apply(*args)
+

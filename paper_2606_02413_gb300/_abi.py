@@ -22,7 +22,7 @@ RAY_STATUS = {1: "EXIT_OUTER", 2: "HIT_INNER", 3: "TAU_STOP", 4: "STEP_LIMIT", 5
 
 # every symbol include/rt.h declares
 EXPORTS = ["rt_default_options", "rt_status_string", "rt_last_error", "rt_create", "rt_destroy",
-           "rt_load_grid", "rt_free_grid", "rt_trace_image", "rt_batch_plan_create", "rt_batch_plan_launch",
+           "rt_load_grid", "rt_free_grid", "rt_trace_image", "rt_backward", "rt_batch_plan_create", "rt_batch_plan_launch",
            "rt_batch_plan_stats", "rt_batch_plan_destroy", "rt_trace_batch", "rt_trace_batch_noalloc",
            "rt_probe_field", "rt_sync", "rt_get_stats"]
 
@@ -92,6 +92,8 @@ def lib():
         L.rt_trace_image.argtypes = [vp, vp, C.POINTER(View), C.POINTER(C.c_double), ip,
                                      C.POINTER(Options), vp, vp, vp]
         L.rt_probe_field.argtypes = [vp, vp, vp, ip, vp, vp]
+        L.rt_backward.argtypes = [vp, vp, C.POINTER(View), C.POINTER(C.c_double), ip, C.POINTER(Options),
+                                  vp, vp, vp, vp, vp]
         L.rt_batch_plan_create.argtypes = [vp, vp, C.POINTER(Request), ip, C.POINTER(Options), C.POINTER(vp)]
         L.rt_batch_plan_launch.argtypes = [vp, vp]
         L.rt_batch_plan_stats.argtypes = [vp, vp, C.POINTER(Stats)]
@@ -100,7 +102,7 @@ def lib():
         L.rt_trace_batch_noalloc.argtypes = [vp, C.POINTER(Request), ip, C.POINTER(Options), vp]
         L.rt_sync.argtypes = [vp, vp]
         L.rt_get_stats.argtypes = [vp, vp, C.POINTER(Stats)]
-        for name in ("rt_create", "rt_destroy", "rt_load_grid", "rt_free_grid", "rt_trace_image",
+        for name in ("rt_create", "rt_destroy", "rt_load_grid", "rt_free_grid", "rt_trace_image", "rt_backward",
                      "rt_batch_plan_create", "rt_batch_plan_launch", "rt_batch_plan_stats",
                      "rt_batch_plan_destroy", "rt_trace_batch", "rt_trace_batch_noalloc", "rt_probe_field",
                      "rt_sync", "rt_get_stats"):

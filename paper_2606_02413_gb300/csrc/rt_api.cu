@@ -12,7 +12,7 @@
 #include <vector>
 
 #include "rt.h"
-#include "rt_bundle.cuh"
+#include "rt_adjoint.cuh"
 
 using namespace rt;
 
@@ -160,6 +160,17 @@ int blocks_per_sm() {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_bundles<NB, M>, kThreads, 0) != cudaSuccess || b < 1)
       b = 1;
+    cached = b;
+  }
+  return cached;
+}
+
+template <int NB>
+int adj_blocks_per_sm() {
+  static int cached = -1;
+  if (cached < 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, adjoint_bundles<NB>, kThreads, 0) != cudaSuccess || b < 1) b = 1;
     cached = b;
   }
   return cached;
@@ -687,6 +698,128 @@ rt_status rt_trace_batch(rt_ctx* ctx, const rt_grid* g, const rt_request* reqs, 
   rt_batch_plan_destroy(p);
   if (st != RT_OK) return st;
   if (e != cudaSuccess) return fail(RT_ERR_CUDA, "rt_trace_batch: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
+rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const double* freqs, int nf, const rt_options* o,
+                      const float* dL_dTb, float* dL_dne, float* dL_dte, float* tb_out, void* stream) {
+  if (!ctx || !g || !freqs || !dL_dTb || !dL_dne || !dL_dte) return fail(RT_ERR_ARG, "rt_backward: NULL argument");
+  rt_status st = check_view(v);
+  if (st != RT_OK) return st;
+  int nb = 0;
+  st = check_options(o, &nb);
+  if (st != RT_OK) return st;
+  if (o->straight || !(nb == 0 || nb == 4))
+    return fail(RT_ERR_UNSUPPORTED, "rt_backward: supports step-wise magnification with 4 neighbours or none");
+  if (nf < 1 || nf > kMaxFreq) return fail(RT_ERR_ARG, "rt_backward: nf = %d (1..%d)", nf, kMaxFreq);
+  for (int i = 0; i < nf; ++i)
+    if (bad_freq(freqs[i])) return fail(RT_ERR_ARG, "frequency %d is not > 0", i);
+  const long npix = (long)v->nx * v->ny;
+  const long total = (long)nf * npix;
+  if (total >= (1L << 31)) return fail(RT_ERR_ARG, "rt_backward: too many rays");
+  const bool mixed = o->precision == RT_MIXED;
+  RT_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // scratch
+  float* tb = nullptr;
+  RayDiag* diag = nullptr;
+  unsigned long long* ck_off = nullptr;
+  Ckpt* ckpt = nullptr;
+  StepRec* rec = nullptr;
+  auto release = [&]() {
+    cudaFree(diag);
+    cudaFree(ck_off);
+    cudaFree(ckpt);
+    cudaFree(rec);
+    if (!tb_out) cudaFree(tb);
+  };
+  cudaError_t e = cudaMalloc(&diag, sizeof(RayDiag) * total);
+  if (e == cudaSuccess && !tb_out) e = cudaMalloc(&tb, sizeof(float) * total);
+  if (e == cudaSuccess) e = cudaMalloc(&ck_off, sizeof(unsigned long long) * (total + 1));
+  if (e != cudaSuccess) {
+    release();
+    return fail(e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "rt_backward: %s", cudaGetErrorString(e));
+  }
+  if (tb_out) tb = tb_out;
+
+  // phase 0: forward with per-ray step counts
+  TraceParams P;
+  std::memset(&P, 0, sizeof P);
+  fill_common(P, g, o);
+  P.view = make_view(*v);
+  P.nf = nf;
+  std::vector<int> order(nf);
+  for (int i = 0; i < nf; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return freqs[a] < freqs[b]; });
+  for (int i = 0; i < nf; ++i) P.freq[i] = make_freq(freqs[order[i]], order[i]);
+  P.tb_out = tb;
+  P.diag = diag;
+  P.counter = ctx->d_counter;
+  P.stats = ctx->d_stats;
+  P.total = (unsigned int)total;
+  auto run_forward = [&]() -> cudaError_t {
+    cudaError_t r = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), s);
+    if (r == cudaSuccess) r = cudaMemsetAsync(ctx->d_stats, 0, 2 * sizeof(unsigned long long), s);
+    if (r == cudaSuccess) r = dispatch_trace(nb, mixed, P, ctx->sm_count, s);
+    return r;
+  };
+  e = run_forward();
+  std::vector<RayDiag> hd(total);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hd.data(), diag, sizeof(RayDiag) * total, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    release();
+    return fail(RT_ERR_CUDA, "rt_backward (forward): %s", cudaGetErrorString(e));
+  }
+  // checkpoint offsets, indexed by ticket (frequency in processing order, pixel)
+  std::vector<unsigned long long> off(total + 1, 0);
+  for (long t = 0; t < total; ++t) {
+    const long fi = t / npix, pix = t - fi * npix;
+    const RayDiag& d = hd[(size_t)order[fi] * npix + pix];
+    const unsigned long long cnt = (d.steps > 0) ? (unsigned long long)((d.steps - 1) / kCkptEvery + 1) : 0ull;
+    off[t + 1] = off[t] + cnt;
+  }
+  const int grid_blocks = ctx->sm_count * (nb == 0 ? adj_blocks_per_sm<0>() : adj_blocks_per_sm<4>());
+  const long slots = (long)grid_blocks * (kThreads / 32) * (32 / (nb + 1));
+  e = cudaMalloc(&ckpt, sizeof(Ckpt) * std::max<unsigned long long>(off[total], 1ull));
+  if (e == cudaSuccess) e = cudaMalloc(&rec, sizeof(StepRec) * slots * (kCkptEvery + 1));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ck_off, off.data(), sizeof(unsigned long long) * (total + 1),
+                                            cudaMemcpyHostToDevice, s);
+  // phase 1: the same forward again, storing checkpoints
+  P.ckpt = ckpt;
+  P.ck_off = ck_off;
+  if (e == cudaSuccess) e = run_forward();
+  // phase 2: reverse sweep
+  if (e == cudaSuccess) e = cudaMemsetAsync(dL_dne, 0, sizeof(float) * (size_t)g->n_r * g->n_t * g->n_p, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dL_dte, 0, sizeof(float) * (size_t)g->n_r * g->n_t * g->n_p, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) {
+    AdjParams A;
+    std::memset(&A, 0, sizeof A);
+    A.G = g->dev;
+    A.h = P.h; A.h2_6 = P.h2_6; A.h_6 = P.h_6; A.h2_12 = P.h2_12; A.hrsun = P.hrsun;
+    A.eta = P.eta; A.eps_fixed = P.eps_fixed; A.tbc_K = P.tbc_K; A.tbc_mode = P.tbc_mode; A.emission = P.emission;
+    A.view = P.view;
+    A.nf = nf;
+    for (int i = 0; i < nf; ++i) A.freq[i] = P.freq[i];
+    A.diag = diag;
+    A.dL_dTb = dL_dTb;
+    A.ckpt = ckpt;
+    A.ck_off = ck_off;
+    A.rec = rec;
+    A.dne = dL_dne;
+    A.dte = dL_dte;
+    A.counter = ctx->d_counter;
+    A.total = (unsigned int)total;
+    if (nb == 0) adjoint_bundles<0><<<grid_blocks, kThreads, 0, s>>>(A);
+    else adjoint_bundles<4><<<grid_blocks, kThreads, 0, s>>>(A);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  release();
+  if (e != cudaSuccess)
+    return fail(e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "rt_backward: %s", cudaGetErrorString(e));
   return RT_OK;
 }
 

@@ -74,6 +74,7 @@ __device__ __forceinline__ float chord_crossing(const Vec& r, const Vec& dr, flo
 // Per-bundle state of the central lane, kept in shared memory so that only
 // the RK4 state lives in registers across the four field evaluations.
 struct BundleState {
+  unsigned int item;                                    // ticket of this ray
   float* out;                                           // T_b of this ray
   RayDiag* dg;                                          // its diagnostics or null
   int step, status;
@@ -180,6 +181,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
           }
           if (valid) {  // a ragged chunk tail has no ray behind the ticket: take another
             // launch (Sec. 3.2): entry point on the outer sphere, k = n(r0) (-o)
+            B.item = item;
             B.kf = P.straight ? 0.f : F->kf;
             B.kap_c = F->kap_c;
             B.ln_f = F->ln_f;
@@ -314,6 +316,19 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
           } else if (step >= P.max_steps) {
             finish(kStepLimit, px, py, pz, B.tb_hi + B.tb_lo);
             done = true;
+          }
+        }
+        if (!done && P.ckpt && (step % kCkptEvery) == 0) {
+          // state at node `step` for the adjoint's recomputation (bounded by the ray's allocation)
+          const unsigned long long slot = P.ck_off[B.item] + (unsigned long long)(step / kCkptEvery);
+          if (slot < P.ck_off[B.item + 1]) {
+            Ckpt& c = P.ckpt[slot];
+            c.r[0] = px; c.r[1] = py; c.r[2] = pz;
+            c.k[0] = kx; c.k[1] = ky; c.k[2] = kz;
+            c.rl[0] = B.rl[0]; c.rl[1] = B.rl[1]; c.rl[2] = B.rl[2];
+            c.kl[0] = B.kl[0]; c.kl[1] = B.kl[1]; c.kl[2] = B.kl[2];
+            c.tau_hi = B.tau_hi; c.tau_lo = B.tau_lo;
+            c.lns_hi = B.lns_hi; c.lns_lo = B.lns_lo;
           }
         }
         if (!done) {

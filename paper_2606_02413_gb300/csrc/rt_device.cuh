@@ -287,6 +287,14 @@ struct ChunkDev {
   int pad;
 };
 
+// Forward state at the start of every kCkptEvery-th central step, written
+// (optionally) by the forward kernel for the adjoint's recomputation.
+constexpr int kCkptEvery = 32;
+struct Ckpt {
+  float r[3], k[3], rl[3], kl[3];
+  float tau_hi, tau_lo, lns_hi, lns_lo;
+};
+
 struct TraceParams {
   GridDev G;
   float h, h2_6, h_6, h2_12, hrsun;  // step and derived constants, hrsun = h R_sun [cm]
@@ -310,6 +318,9 @@ struct TraceParams {
   unsigned int* counter;            // work queue ticket (zeroed before launch)
   unsigned long long* stats;        // [0] ray steps, [1] rays
   unsigned int total;               // tickets
+  // optional checkpoints (image mode): ray t owns ckpt[ck_off[t] .. ck_off[t+1])
+  Ckpt* ckpt;
+  const unsigned long long* ck_off;
 };
 
 }  // namespace rt
