@@ -184,6 +184,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "plain"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -270,6 +272,57 @@ def main():
                "h2d_bytes_per_step": int(ne_h.numel() * 4 + te_h.numel() * 4),
                "d2h_bytes_per_step": int(tb_h.numel() * 4), "seconds_per_step": dt}
 
+    # the other forms on the same workload: plain FP32, and the batched
+    # (graph-captured persistent) launch of the same 16 maps
+    forms = {"mixed": {"ms": total_ms / args.steps, "ray_steps_per_s": value / ws, "maps_per_s": maps_per_s / ws}}
+    if not args.no_forms:
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b)
+        other = rt.RT_PLAIN_F32 if prec == rt.RT_MIXED else rt.RT_MIXED
+        o2 = rt.options(precision=other)
+        ms2 = timed(lambda: ctx.trace_image(grid, v, f, o2, out=out))
+        st2 = ctx.stats()
+        forms["plain" if other == rt.RT_PLAIN_F32 else "mixed_alt"] = {
+            "ms": ms2, "ray_steps_per_s": st2["ray_steps"] / (ms2 / 1e3), "maps_per_s": len(f) / (ms2 / 1e3)}
+        plan = ctx.batch_plan(grid, [cs.Request(v, f)], opts)
+        ms3 = timed(plan.launch)
+        st3 = plan.stats()
+        forms["batched_mixed"] = {"ms": ms3, "ray_steps_per_s": st3["ray_steps"] / (ms3 / 1e3),
+                                  "maps_per_s": len(f) / (ms3 / 1e3), "launch": "CUDA graph, longest-first chunks"}
+        plan.destroy()
+
+    # adjoint/forward time ratio on the differentiation workload
+    adjoint = None
+    if not args.no_adjoint:
+        ga, va, fa = cs.adjoint_workload()
+        grid_a = ctx.load(ga)
+        adjoint = {"workload": "Newkirk 128x90x180 grid, 256x256 x 8 freq 40-400 MHz, 4 neighbours"}
+        for nm, pr in (("mixed", rt.RT_MIXED), ("plain", rt.RT_PLAIN_F32)):
+            oa = rt.options(precision=pr)
+            ctx.trace_image(grid_a, va, fa, oa)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tbf = ctx.trace_image(grid_a, va, fa, oa)
+            torch.cuda.synchronize()
+            tf = time.perf_counter() - t0
+            wgt = torch.ones_like(tbf)
+            ctx.backward(grid_a, va, fa, wgt, oa)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.backward(grid_a, va, fa, wgt, oa)
+            torch.cuda.synchronize()
+            tbk = time.perf_counter() - t0
+            adjoint[nm] = {"forward_s": tf, "backward_s": tbk, "ratio": tbk / tf}
+        grid_a.free()
+
     peaks, peak_src = load_peaks()
     clk = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
@@ -296,7 +349,8 @@ def main():
                            "rays_per_step": int(stats["rays"]) * ws, "l2": "inputs larger than L2 "
                            "(1.06 GB corner-packed grid, 4.19 M rays/step)", "parallelism": f"weak x{ws}"},
                 "maps_per_s": maps_per_s, "ray_steps_per_step": all_steps / args.steps,
-                "adjoint_forward_ratio": None, "gpu_launches": args.steps,
+                "adjoint_forward_ratio": adjoint["mixed"]["ratio"] if adjoint else None,
+                "adjoint": adjoint, "forms": forms, "gpu_launches": args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "peaks_source": peak_src}
         print(json.dumps(line), flush=True)
