@@ -175,6 +175,37 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case(name):
+    """One launch of a named case, small enough for an ncu capture.
+    fwd-WxHxF: the headline corona, a WxH view over +-3 R_sun at 60 and 300
+    MHz, compensated form.  adj-WxHxF: rt_backward on the 128x90x180
+    differentiation corona, a WxH view over +-2.5 R_sun at 60 and 200 MHz
+    (adj-256x256x8: the full differentiation workload), dL/dT_b = 1."""
+    import torch
+
+    import corona_synth as cs
+    from paper_2606_02413_gb300 import build as rt_build
+    rt_build.build()
+    import paper_2606_02413_gb300 as rt
+    ctx = rt.Context(0)
+    kind, dims = name.split("-")
+    nx, ny, nf = (int(x) for x in dims.split("x"))
+    if kind == "fwd":
+        g, _, _ = cs.global_workload()
+        grid = ctx.load(g)
+        v = cs.View(0.0, 0.0, nx, ny, -3.0, 3.0, -3.0, 3.0)
+        ctx.trace_image(grid, v, [60e6, 300e6][:nf], rt.options(precision=rt.RT_MIXED))
+    else:
+        g, v, f = cs.adjoint_workload()
+        grid = ctx.load(g)
+        if nf != len(f):
+            v = cs.View(0.0, 0.0, nx, ny, -2.5, 2.5, -2.5, 2.5)
+            f = [60e6, 200e6][:nf]
+        ctx.backward(grid, v, f, torch.ones((len(f), v.ny, v.nx), device="cuda"), rt.options(precision=rt.RT_MIXED))
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": name, "stats": ctx.stats()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -185,10 +216,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--profile-case", default=None,
+                    choices=["fwd-128x128x2", "fwd-256x256x2", "adj-64x64x2", "adj-256x256x8"],
+                    help="run one launch of a small named case (for ncu captures) and exit")
     ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_case:
+        run_profile_case(args.profile_case)
         return
 
     import torch
