@@ -648,7 +648,9 @@ int orc_trace(const orc_field* F, const orc_view* V, const double* freqs, int nf
     const int px = pixels ? pixels[t % npix] : int(t % npix);
     Jitter J;
     J.amp = o->jitter;
-    J.state = (o->jitter_seed ^ (0x9E3779B97F4A7C15ull * (unsigned long long)(t + 1))) | 1ull;
+    // the seed is spread over all bits first, so that seeds differing only in
+    // bit 0 still give different streams after the final | 1
+    J.state = ((o->jitter_seed * 0xBF58476D1CE4E5B9ull) ^ (0x9E3779B97F4A7C15ull * (unsigned long long)(t + 1))) | 1ull;
     RayCtx C{F, o, freqs[fi], o->dtau, &J};
     PlainNodes nodes{F};
     PixelGeom g = pixel_centre(*V, px);
