@@ -110,6 +110,9 @@ typedef struct {
   int emission;     /* 1: free-free j and kappa; 0: j = kappa = 0 (I S = const)     */
   int straight;     /* 1: straight lines of sight, n = 1, no magnification           */
   int precision;    /* RT_PLAIN_F32 or RT_MIXED (compensated state and accumulators) */
+  int tile;         /* launch: rt_trace_image takes pixels in tile x tile blocks (2..32); */
+                    /* 0 = row by row.  Results do not depend on it.                   */
+  int blocks_per_sm;/* launch: persistent blocks per SM; 0 = as many as fit              */
 } rt_options;
 
 /* Optional per-ray diagnostics (28 bytes). */

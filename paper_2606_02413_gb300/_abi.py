@@ -42,7 +42,8 @@ class Options(C.Structure):
     _fields_ = [("dtau", C.c_double), ("s_mode", C.c_int), ("n_nb", C.c_int), ("eps_mode", C.c_int),
                 ("eta", C.c_double), ("delta", C.c_double), ("tau_stop", C.c_double),
                 ("max_steps", C.c_int), ("tbc_mode", C.c_int), ("tbc_K", C.c_double),
-                ("emission", C.c_int), ("straight", C.c_int), ("precision", C.c_int)]
+                ("emission", C.c_int), ("straight", C.c_int), ("precision", C.c_int),
+                ("tile", C.c_int), ("blocks_per_sm", C.c_int)]
 
 
 class RayDiag(C.Structure):

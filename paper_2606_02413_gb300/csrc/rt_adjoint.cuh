@@ -341,8 +341,8 @@ __global__ void __launch_bounds__(kThreads) adjoint_bundles(const __grid_constan
           exhausted = true;
           need = false;
         } else {
-          const int fi = item / P.view.npix;
-          const int pix = item - fi * P.view.npix;
+          const int fi = item / P.view.tickets;
+          const int pix = item - fi * P.view.tickets;
           const FreqDev& F = P.freq[fi];
           const size_t o = (size_t)F.out_slab * P.view.npix + pix;
           const RayDiag d = P.diag[o];

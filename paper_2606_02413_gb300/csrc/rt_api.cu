@@ -153,12 +153,12 @@ __global__ void probe_field(const GridDev G, const float* __restrict__ xyz, int 
   out[5 * i + 4] = s.gz;
 }
 
-template <int NB, bool M>
+template <int NB, bool M, bool T>
 int blocks_per_sm() {
   static int cached = -1;
   if (cached < 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_bundles<NB, M>, kThreads, 0) != cudaSuccess || b < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_bundles<NB, M, T>, kThreads, 0) != cudaSuccess || b < 1)
       b = 1;
     cached = b;
   }
@@ -176,19 +176,31 @@ int adj_blocks_per_sm() {
   return cached;
 }
 
-template <int NB, bool M>
+template <int NB, bool M, bool T>
 cudaError_t launch_trace(const TraceParams& P, int sm_count, cudaStream_t s) {
-  const int grid = sm_count * blocks_per_sm<NB, M>();
-  trace_bundles<NB, M><<<grid, kThreads, 0, s>>>(P);
+  const int fit = blocks_per_sm<NB, M, T>();
+  const int per_sm = (P.blocks_per_sm > 0) ? std::min(P.blocks_per_sm, fit) : fit;
+  const int grid = sm_count * per_sm;
+  trace_bundles<NB, M, T><<<grid, kThreads, 0, s>>>(P);
   return cudaGetLastError();
 }
 
-cudaError_t dispatch_trace(int nb, bool mixed, const TraceParams& P, int sm, cudaStream_t s) {
+// nb: neighbour lanes per bundle (0 = magnification off); tube: persistent
+// neighbours (tube mode) instead of the step-wise retrace
+cudaError_t dispatch_trace(int nb, bool mixed, const TraceParams& P, int sm, cudaStream_t s, bool tube = false) {
+  if (tube) {
+    switch (nb) {
+      case 2: return mixed ? launch_trace<2, true, true>(P, sm, s) : launch_trace<2, false, true>(P, sm, s);
+      case 4: return mixed ? launch_trace<4, true, true>(P, sm, s) : launch_trace<4, false, true>(P, sm, s);
+      case 8: return mixed ? launch_trace<8, true, true>(P, sm, s) : launch_trace<8, false, true>(P, sm, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (nb) {
-    case 0: return mixed ? launch_trace<0, true>(P, sm, s) : launch_trace<0, false>(P, sm, s);
-    case 2: return mixed ? launch_trace<2, true>(P, sm, s) : launch_trace<2, false>(P, sm, s);
-    case 4: return mixed ? launch_trace<4, true>(P, sm, s) : launch_trace<4, false>(P, sm, s);
-    case 8: return mixed ? launch_trace<8, true>(P, sm, s) : launch_trace<8, false>(P, sm, s);
+    case 0: return mixed ? launch_trace<0, true, false>(P, sm, s) : launch_trace<0, false, false>(P, sm, s);
+    case 2: return mixed ? launch_trace<2, true, false>(P, sm, s) : launch_trace<2, false, false>(P, sm, s);
+    case 4: return mixed ? launch_trace<4, true, false>(P, sm, s) : launch_trace<4, false, false>(P, sm, s);
+    case 8: return mixed ? launch_trace<8, true, false>(P, sm, s) : launch_trace<8, false, false>(P, sm, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -443,7 +455,9 @@ static rt_status check_options(const rt_options* o, int* nb_out) {
   if (o->eps_mode != 0 && o->eps_mode != 1) return fail(RT_ERR_ARG, "eps_mode %d", o->eps_mode);
   if (o->precision != RT_PLAIN_F32 && o->precision != RT_MIXED) return fail(RT_ERR_ARG, "precision %d", o->precision);
   if (o->tbc_mode != 0 && o->tbc_mode != 1) return fail(RT_ERR_ARG, "tbc_mode %d", o->tbc_mode);
-  if (o->s_mode == RT_TUBE && !o->straight) return fail(RT_ERR_UNSUPPORTED, "tube mode is not built yet");
+  if (o->tile != 0 && (o->tile < 2 || o->tile > 32)) return fail(RT_ERR_ARG, "tile %d (0 or 2..32)", o->tile);
+  if (o->blocks_per_sm < 0) return fail(RT_ERR_ARG, "blocks_per_sm %d", o->blocks_per_sm);
+  if (o->s_mode == RT_TUBE && !(o->delta > 0.0)) return fail(RT_ERR_ARG, "tube mode needs delta > 0");
   *nb_out = (o->straight || o->s_mode == RT_MAG_OFF) ? 0 : o->n_nb;
   return RT_OK;
 }
@@ -471,8 +485,19 @@ ViewDev make_view(const rt_view& v) {
   V.x0 = (float)v.x0; V.dx = (float)((v.x1 - v.x0) / v.nx);
   V.y0 = (float)v.y0; V.dy = (float)((v.y1 - v.y0) / v.ny);
   V.nx = v.nx;
+  V.ny = v.ny;
   V.npix = v.nx * v.ny;
+  V.tile = 0;
+  V.tiles_x = 0;
+  V.tickets = V.npix;
   return V;
+}
+
+void set_tiles(ViewDev& V, int tile) {
+  if (tile <= 0) return;
+  V.tile = tile;
+  V.tiles_x = (V.nx + tile - 1) / tile;
+  V.tickets = V.tiles_x * ((V.ny + tile - 1) / tile) * tile * tile;
 }
 
 FreqDev make_freq(double f, int slab) {
@@ -502,9 +527,14 @@ void fill_common(TraceParams& P, const rt_grid* g, const rt_options* o) {
   P.tbc_K = (float)o->tbc_K;
   P.emission = o->emission;
   P.straight = o->straight;
+  P.blocks_per_sm = o->blocks_per_sm;
+  P.tube_delta = (float)o->delta;
+  P.inv_delta2 = (float)(1.0 / (o->delta * o->delta));
 }
 
 bool bad_freq(double f) { return !(f > 0.0) || !std::isfinite(f); }
+
+bool is_tube(const rt_options* o) { return o->s_mode == RT_TUBE && !o->straight; }
 
 // Estimated RK4 steps of a ray with impact parameter b (in units of h):
 // the entry chord, cut at the turning radius r_c where the shell-mean
@@ -547,6 +577,8 @@ rt_status rt_trace_image(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const 
   std::memset(&P, 0, sizeof P);
   fill_common(P, g, o);
   P.view = make_view(*v);
+  set_tiles(P.view, o->tile);
+  if ((long)nf * P.view.tickets >= (1L << 31)) return fail(RT_ERR_ARG, "rt_trace_image: too many rays");
   P.nf = nf;
   // lowest frequencies first: their rays turn high and tend to be longest
   std::vector<int> order(nf);
@@ -557,13 +589,13 @@ rt_status rt_trace_image(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const 
   P.diag = reinterpret_cast<RayDiag*>(diag);
   P.counter = ctx->d_counter;
   P.stats = ctx->d_stats;
-  P.total = (unsigned int)total;
+  P.total = (unsigned int)((long)nf * P.view.tickets);
 
   RT_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   RT_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), s));
   RT_CUDA(cudaMemsetAsync(ctx->d_stats, 0, 2 * sizeof(unsigned long long), s));
-  RT_CUDA(dispatch_trace(nb, o->precision == RT_MIXED, P, ctx->sm_count, s));
+  RT_CUDA(dispatch_trace(nb, o->precision == RT_MIXED, P, ctx->sm_count, s, is_tube(o)));
   return RT_OK;
 }
 
@@ -656,7 +688,7 @@ rt_status rt_batch_plan_create(rt_ctx* ctx, const rt_grid* g, const rt_request* 
   if (e == cudaSuccess) {
     cudaError_t e1 = cudaMemsetAsync(p->counter, 0, sizeof(unsigned int), p->cap);
     cudaError_t e2 = cudaMemsetAsync(p->stats, 0, 2 * sizeof(unsigned long long), p->cap);
-    cudaError_t e3 = dispatch_trace(nb, o->precision == RT_MIXED, P, ctx->sm_count, p->cap);
+    cudaError_t e3 = dispatch_trace(nb, o->precision == RT_MIXED, P, ctx->sm_count, p->cap, is_tube(o));
     e = cudaStreamEndCapture(p->cap, &p->graph);
     if (e == cudaSuccess) e = (e1 != cudaSuccess) ? e1 : (e2 != cudaSuccess) ? e2 : e3;
   }
@@ -709,7 +741,7 @@ rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const dou
   int nb = 0;
   st = check_options(o, &nb);
   if (st != RT_OK) return st;
-  if (o->straight || !(nb == 0 || nb == 4))
+  if (o->straight || o->s_mode == RT_TUBE || !(nb == 0 || nb == 4))
     return fail(RT_ERR_UNSUPPORTED, "rt_backward: supports step-wise magnification with 4 neighbours or none");
   if (nf < 1 || nf > kMaxFreq) return fail(RT_ERR_ARG, "rt_backward: nf = %d (1..%d)", nf, kMaxFreq);
   for (int i = 0; i < nf; ++i)
@@ -955,7 +987,7 @@ extern "C" rt_status rt_trace_batch_noalloc(const rt_grid* g, const rt_request* 
   P.counter = reinterpret_cast<unsigned int*>(D.scratch);
   P.stats = reinterpret_cast<unsigned long long*>(D.scratch + 8);
   P.total = (unsigned int)(cands.size() * kChunk);
-  RT_CUDA(dispatch_trace(nb, o->precision == RT_MIXED, P, D.sm_count, s));
+  RT_CUDA(dispatch_trace(nb, o->precision == RT_MIXED, P, D.sm_count, s, is_tube(o)));
   return RT_OK;
 }
 

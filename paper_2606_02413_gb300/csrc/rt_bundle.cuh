@@ -85,8 +85,34 @@ struct BundleState {
   float t[3], e1[3], e2[3], eps;                        // basis of the retraced step
   float g0[3];                                          // central G of that step (2 neighbours)
   float alpha, pc[3];                                   // clipped last step
+  // tube mode: launch data the neighbour lanes read to start their rays
+  const ViewDev* view;
+  float u, v, sc, nc, nec, kn2;
+  int tube_ok;
   unsigned long long steps_done, rays_done;
 };
+
+// Tube-mode image-plane offset of neighbour role q (Sec. 2 persistent
+// reading): +-e_u, +-e_v, and with 8 neighbours the 45-degree diagonals.
+template <int NB>
+__device__ __forceinline__ void tube_offset(int q, float& a, float& b) {
+  const float s2 = 0.70710678118654752f;
+  if (NB == 2) {
+    a = (q == 1) ? 1.f : 0.f;
+    b = (q == 1) ? 0.f : 1.f;
+    return;
+  }
+  switch (q) {
+    case 1: a = 1.f; b = 0.f; break;
+    case 2: a = -1.f; b = 0.f; break;
+    case 3: a = 0.f; b = 1.f; break;
+    case 4: a = 0.f; b = -1.f; break;
+    case 5: a = s2; b = s2; break;
+    case 6: a = -s2; b = -s2; break;
+    case 7: a = -s2; b = s2; break;
+    default: a = s2; b = -s2; break;
+  }
+}
 
 template <bool kComp>
 __device__ __forceinline__ void acc_add(float& hi, float& lo, float x) {
@@ -100,8 +126,13 @@ __device__ __forceinline__ void acc_add(float& hi, float& lo, float x) {
   }
 }
 
-template <int NB, bool kMixed>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __grid_constant__ TraceParams P) {
+// kTube: the neighbours are persistent rays launched at image-plane offsets
+// +-delta and integrated in lock-step with the central ray; each neighbour
+// lane carries its offset (dr, dk) from the central ray, updated with the
+// difference of RK4 increments, and S = |det[d1, d2, t]| is taken after every
+// step with central differences d_j of those offsets (S_0 = delta^2).
+template <int NB, bool kMixed, bool kTube>
+__global__ void __launch_bounds__(kThreads, kTube ? kMinBlocksTube : kMinBlocks) trace_bundles(const __grid_constant__ TraceParams P) {
   constexpr int L = NB + 1;
   constexpr int BPW = 32 / L;
   __shared__ BundleState S[kThreads / 32][BPW];
@@ -123,6 +154,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
   int phase = 0;          // central: 0 needs work, 1 stepping, 2 final (clipped) segment
   bool emitted = false;   // central: its neighbours retrace a step this iteration
   bool exhausted = !central;
+  bool fresh = false;     // central (tube mode): a ray started in this iteration
+  // tube neighbours (mixed form): rounding carried by the offset accumulation
+  float lpx = 0.f, lpy = 0.f, lpz = 0.f, lkx = 0.f, lky = 0.f, lkz = 0.f;
 
   auto finish = [&](int st, float ex, float ey, float ez, float tb_val) {
     *B.out = tb_val;
@@ -171,8 +205,17 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
             B.out = M.out + pix;
             B.dg = M.diag ? M.diag + pix : nullptr;
           } else {
-            const int fi = item / P.view.npix;
-            pix = item - fi * P.view.npix;
+            const int fi = item / P.view.tickets;
+            const int t = item - fi * P.view.tickets;
+            if (P.view.tile > 0) {  // tile-major walk; tickets past the image edge carry no ray
+              const int T = P.view.tile, tt = T * T;
+              const int tile = t / tt, w = t - tile * tt;
+              const int ix = (tile % P.view.tiles_x) * T + w % T, iy = (tile / P.view.tiles_x) * T + w / T;
+              valid = ix < P.view.nx && iy < P.view.ny;
+              pix = valid ? iy * P.view.nx + ix : 0;
+            } else {
+              pix = t;
+            }
             V = &P.view;
             F = &P.freq[fi];
             const size_t o = (size_t)F->out_slab * P.view.npix + pix;
@@ -195,7 +238,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
             const float R = P.G.r_max;
             const float b2 = fmaf(u, u, v * v);
             bool ok = b2 < R * R;
-            float nn = 1.f;
+            float nn = 1.f, ne0 = 0.f;
             float r0x = 0.f, r0y = 0.f, r0z = 0.f;
             if (ok) {
               const float s = sqrtf(fmaf(R, R, -b2));
@@ -204,6 +247,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
               r0z = fmaf(u, V->euz, fmaf(v, V->evz, s * V->oz));
               if (!P.straight) {
                 const Sample s0 = eval_field(P.G, r0x, r0y, r0z, false);
+                ne0 = s0.ne;
                 const float n2 = fmaf(F->kn2, s0.ne, 1.f);
                 ok = n2 > 0.f;
                 nn = ok ? sqrtf(n2) : 0.f;
@@ -216,6 +260,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
               kx = -nn * V->ox; ky = -nn * V->oy; kz = -nn * V->oz;
               phase = 1;
               need = false;
+              if (kTube) {
+                B.view = V;
+                B.u = u; B.v = v;
+                B.sc = sqrtf(fmaf(R, R, -b2));
+                B.nc = nn;
+                B.nec = ne0;
+                B.kn2 = F->kn2;
+                fresh = true;
+              }
             }
           }
         }
@@ -224,14 +277,79 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
     }
     if (!__any_sync(kFull, phase != 0)) break;
 
+    if (kTube) {
+      // neighbours of a new bundle launch from their offset pixel positions:
+      // entry offsets and wave-vector offsets formed without cancellation
+      const bool fr = __shfl_sync(kFull, fresh ? 1 : 0, base) != 0;
+      const float ex = __shfl_sync(kFull, px, base), ey = __shfl_sync(kFull, py, base),
+                  ez = __shfl_sync(kFull, pz, base);  // the central entry point
+      __syncwarp();
+      bool ok = true;
+      if (used && q > 0 && fr) {
+        float a, b;
+        tube_offset<NB>(q, a, b);
+        const ViewDev& V = *B.view;
+        const float du = P.tube_delta * a, dv = P.tube_delta * b;
+        const float R = P.G.r_max;
+        const float un = B.u + du, vn = B.v + dv;
+        const float b2n = fmaf(un, un, vn * vn);
+        ok = b2n < R * R;
+        if (ok) {
+          const float sn = sqrtf(fmaf(R, R, -b2n));
+          const float dsv = -(2.f * fmaf(B.u, du, B.v * dv) + fmaf(du, du, dv * dv)) / (sn + B.sc);
+          const float ox = fmaf(du, V.eux, fmaf(dv, V.evx, dsv * V.ox));
+          const float oy = fmaf(du, V.euy, fmaf(dv, V.evy, dsv * V.oy));
+          const float oz = fmaf(du, V.euz, fmaf(dv, V.evz, dsv * V.oz));
+          px = ox; py = oy; pz = oz;
+          lpx = lpy = lpz = lkx = lky = lkz = 0.f;
+          float nn = 1.f;
+          if (!P.straight) {
+            const Sample s0 = eval_field_off(P.G, base_point(P.G, ex, ey, ez), ox, oy, oz, false);
+            const float n2 = fmaf(B.kn2, s0.ne, 1.f);
+            ok = n2 > 0.f;
+            nn = ok ? sqrtf(n2) : 0.f;
+            const float dn = ok ? B.kn2 * (s0.ne - B.nec) / (nn + B.nc) : 0.f;
+            kx = -dn * V.ox; ky = -dn * V.oy; kz = -dn * V.oz;
+          } else {
+            kx = ky = kz = 0.f;
+          }
+        }
+        has_seed = ok;
+      }
+      const unsigned okmask = __ballot_sync(kFull, ok);
+      if (central && fresh) {
+        const unsigned mine = ((1u << (NB + 1)) - 1u) << lane;
+        B.tube_ok = ((okmask & mine) == mine) ? 1 : 0;
+        fresh = false;
+      }
+    }
+
     // ------------------------------------------------------------ RK4
-    // central lanes step (phase 1); neighbour lanes retrace (has_seed)
+    // central lanes step (phase 1); neighbour lanes retrace (has_seed), or
+    // in tube mode step their own rays from the central state + offsets
     const float kf_lane = __shfl_sync(kFull, (central && phase != 0) ? B.kf : 0.f, base);
-    const bool work = central ? (phase == 1) : has_seed;
+    const int bphase = __shfl_sync(kFull, phase, base);
+    const bool work = central ? (phase == 1) : (kTube ? (has_seed && bphase == 1) : has_seed);
     Rk4Out o;
     o.Gx = o.Gy = o.Gz = o.Ax = o.Ay = o.Az = 0.f;
     o.ne1 = o.te1 = 0.f;
-    if (work) o = rk4_step(P.G, kf_lane, h, px, py, pz, kx, ky, kz, central);
+    if (kTube) {
+      // every ray of the bundle steps about the central node (b, its low part l)
+      float lx = 0.f, ly = 0.f, lz = 0.f;
+      if (kMixed && central) { lx = B.rl[0]; ly = B.rl[1]; lz = B.rl[2]; }
+      const float cpx = __shfl_sync(kFull, px, base), cpy = __shfl_sync(kFull, py, base),
+                  cpz = __shfl_sync(kFull, pz, base);
+      const float ckx = __shfl_sync(kFull, kx, base), cky = __shfl_sync(kFull, ky, base),
+                  ckz = __shfl_sync(kFull, kz, base);
+      lx = __shfl_sync(kFull, lx, base); ly = __shfl_sync(kFull, ly, base); lz = __shfl_sync(kFull, lz, base);
+      if (work) {
+        const BasePoint bp = base_point(P.G, cpx, cpy, cpz);
+        o = rk4_step_base(P.G, kf_lane, h, bp, lx, ly, lz, ckx, cky, ckz, central ? 0.f : px, central ? 0.f : py,
+                          central ? 0.f : pz, central ? 0.f : kx, central ? 0.f : ky, central ? 0.f : kz, central);
+      }
+    } else if (work) {
+      o = rk4_step(P.G, kf_lane, h, px, py, pz, kx, ky, kz, central);
+    }
     if (central && phase == 2) {  // the clip point closes the path
       const Sample s = eval_field(P.G, B.pc[0], B.pc[1], B.pc[2], true);
       o.ne1 = s.ne;
@@ -240,8 +358,47 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
 
     // ------------------------------------------------- neighbour exchange
     // raw separations: NB >= 4: D_j = G_{+j} - G_{-j}; NB == 2: G_j
+    // (tube mode: the offsets after this step; central differences for 4, 8)
     Vec d1{0.f, 0.f, 0.f}, d2{0.f, 0.f, 0.f}, d3{0.f, 0.f, 0.f}, d4{0.f, 0.f, 0.f};
-    if (NB == 2) {
+    if (kTube) {
+      const float gcx = __shfl_sync(kFull, o.Gx, base), gcy = __shfl_sync(kFull, o.Gy, base),
+                  gcz = __shfl_sync(kFull, o.Gz, base);
+      const float acx = __shfl_sync(kFull, o.Ax, base), acy = __shfl_sync(kFull, o.Ay, base),
+                  acz = __shfl_sync(kFull, o.Az, base);
+      if (work && !central) {
+        // offset update: d(dr) = h dk + h^2/6 (G_nb - G_c), d(dk) = h/6 (A_nb - A_c); the
+        // increments are ~1e-6 of the offsets, so the mixed form carries their rounding
+        const float ipx = fmaf(h, kx, P.h2_6 * (o.Gx - gcx)), ipy = fmaf(h, ky, P.h2_6 * (o.Gy - gcy)),
+                    ipz = fmaf(h, kz, P.h2_6 * (o.Gz - gcz));
+        const float ikx = P.h_6 * (o.Ax - acx), iky = P.h_6 * (o.Ay - acy), ikz = P.h_6 * (o.Az - acz);
+        if (kMixed) {
+          float t;
+          two_sum(px, ipx + lpx, t, lpx); px = t;
+          two_sum(py, ipy + lpy, t, lpy); py = t;
+          two_sum(pz, ipz + lpz, t, lpz); pz = t;
+          two_sum(kx, ikx + lkx, t, lkx); kx = t;
+          two_sum(ky, iky + lky, t, lky); ky = t;
+          two_sum(kz, ikz + lkz, t, lkz); kz = t;
+        } else {
+          px += ipx; py += ipy; pz += ipz;
+          kx += ikx; ky += iky; kz += ikz;
+        }
+      }
+      if (NB == 2) {
+        d1 = {__shfl_sync(kFull, px, base + 1), __shfl_sync(kFull, py, base + 1), __shfl_sync(kFull, pz, base + 1)};
+        d2 = {__shfl_sync(kFull, px, base + 2), __shfl_sync(kFull, py, base + 2), __shfl_sync(kFull, pz, base + 2)};
+      } else {
+        const float dx = 0.5f * (px - __shfl_down_sync(kFull, px, 1));
+        const float dy = 0.5f * (py - __shfl_down_sync(kFull, py, 1));
+        const float dz = 0.5f * (pz - __shfl_down_sync(kFull, pz, 1));
+        d1 = {__shfl_sync(kFull, dx, base + 1), __shfl_sync(kFull, dy, base + 1), __shfl_sync(kFull, dz, base + 1)};
+        d2 = {__shfl_sync(kFull, dx, base + 3), __shfl_sync(kFull, dy, base + 3), __shfl_sync(kFull, dz, base + 3)};
+        if (NB == 8) {
+          d3 = {__shfl_sync(kFull, dx, base + 5), __shfl_sync(kFull, dy, base + 5), __shfl_sync(kFull, dz, base + 5)};
+          d4 = {__shfl_sync(kFull, dx, base + 7), __shfl_sync(kFull, dy, base + 7), __shfl_sync(kFull, dz, base + 7)};
+        }
+      }
+    } else if (NB == 2) {
       d1 = {__shfl_sync(kFull, o.Gx, base + 1), __shfl_sync(kFull, o.Gy, base + 1), __shfl_sync(kFull, o.Gz, base + 1)};
       d2 = {__shfl_sync(kFull, o.Gx, base + 2), __shfl_sync(kFull, o.Gy, base + 2), __shfl_sync(kFull, o.Gz, base + 2)};
     } else if (NB >= 4) {
@@ -261,7 +418,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
     bool emit = false;
     Vec sr{0.f, 0.f, 0.f}, sk{0.f, 0.f, 0.f}, sa{0.f, 0.f, 0.f}, sb{0.f, 0.f, 0.f};
     if (central && phase != 0) {
-      if (emitted && NB > 0) {  // M of the step the neighbours just retraced (Eqs. 9-11)
+      if (!kTube && emitted && NB > 0) {  // M of the step the neighbours just retraced (Eqs. 9-11)
         const Vec tp{B.t[0], B.t[1], B.t[2]};
         const Vec e1p{B.e1[0], B.e1[1], B.e1[2]}, e2p{B.e2[0], B.e2[1], B.e2[2]};
         Vec c1, c2;
@@ -344,7 +501,19 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
           const float d2n = dot3(dr, dr);
           const float ids = rsqrtf(d2n);
           const Vec tp{dr.x * ids, dr.y * ids, dr.z * ids};
-          if (NB > 0) {
+          if (kTube) {
+            // S_{i+1} = |det[d1, d2, t^i]| (8: mean of the two pairs), ln(S / delta^2)
+            if (B.tube_ok) {
+              const float cx = d1.y * d2.z - d1.z * d2.y, cy = d1.z * d2.x - d1.x * d2.z, cz = d1.x * d2.y - d1.y * d2.x;
+              float S = fabsf(fmaf(tp.x, cx, fmaf(tp.y, cy, tp.z * cz)));
+              if (NB == 8) {
+                const float gx = d3.y * d4.z - d3.z * d4.y, gy = d3.z * d4.x - d3.x * d4.z, gz = d3.x * d4.y - d3.y * d4.x;
+                S = 0.5f * (S + fabsf(fmaf(tp.x, gx, fmaf(tp.y, gy, tp.z * gz))));
+              }
+              B.lns_hi = __logf(S * P.inv_delta2);
+              B.lns_lo = 0.f;
+            }
+          } else if (NB > 0) {
             Vec e1p, e2p;
             basis(tp, e1p, e2p);
             const float eps = (P.eps_fixed > 0.f) ? P.eps_fixed : P.eta * (d2n * ids);
@@ -403,7 +572,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) trace_bundles(const __gr
     }
 
     // ------------------------------------------------- seed broadcast
-    if (NB > 0) {
+    if (!kTube && NB > 0) {
       const bool e = __shfl_sync(kFull, emit ? 1 : 0, base) != 0;
       const float bx = __shfl_sync(kFull, sr.x, base), by = __shfl_sync(kFull, sr.y, base),
                   bz = __shfl_sync(kFull, sr.z, base);

@@ -11,9 +11,10 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxFreq = 64;
 constexpr int kThreads = 128;
 #ifndef RT_MIN_BLOCKS
-#define RT_MIN_BLOCKS 1
+#define RT_MIN_BLOCKS 8
 #endif
-constexpr int kMinBlocks = RT_MIN_BLOCKS;  // __launch_bounds__ occupancy target
+constexpr int kMinBlocks = RT_MIN_BLOCKS;  // __launch_bounds__ occupancy target: 8 x 128 threads per SM
+constexpr int kMinBlocksTube = 6;          // tube bundles: the offset evaluation needs more registers
 
 // ------------------------------------------------------------------ grid
 // Cells are corner-packed: cell (i, j, k) stores the 8 node values of its
@@ -65,21 +66,70 @@ __device__ __forceinline__ float atan2_grid(float y, float x) {
 //   grad f = f_r r_hat + f_theta theta_hat / r + f_phi phi_hat / (r sin theta).
 // T_e is interpolated with the same weights when want_te (a per-lane flag:
 // only the T_e loads diverge, the evaluation itself stays warp-uniform).
-__device__ __forceinline__ Sample eval_field(const GridDev& G, float x, float y, float z, bool want_te) {
+// sample_cell does the corner loads, the interpolation and the chain rule
+// for cell (i, j, k) at fractions (u, v, w) of the point (x, y, z).
+__device__ __forceinline__ Sample sample_cell(const GridDev& G, int i, int j, int k, float u, float v, float w,
+                                              float tsel, float inv_dr, float x, float y, float z,
+                                              float inv_r, float rho, float inv_rho, bool want_te) {
   Sample s;
+  const int cell = (i * (G.n_t - 1) + j) * G.n_p + k;
+  const float4 c0 = __ldg(G.ne + 2 * cell);      // (000, 001, 010, 011)
+  const float4 c1 = __ldg(G.ne + 2 * cell + 1);  // (100, 101, 110, 111)
+  const float d00 = c0.y - c0.x, d01 = c0.w - c0.z, d10 = c1.y - c1.x, d11 = c1.w - c1.z;
+  const float a00 = fmaf(w, d00, c0.x), a01 = fmaf(w, d01, c0.z);
+  const float a10 = fmaf(w, d10, c1.x), a11 = fmaf(w, d11, c1.z);
+  const float e0 = a01 - a00, e1 = a11 - a10;
+  const float b0 = fmaf(v, e0, a00), b1 = fmaf(v, e1, a10);
+  const float fu = b1 - b0;
+  s.ne = fmaf(u, fu, b0);
+  const float fv = fmaf(u, e1 - e0, e0);
+  const float g0 = fmaf(v, d01 - d00, d00), g1 = fmaf(v, d11 - d10, d10);
+  const float fw = fmaf(u, g1 - g0, g0);
+
+  const float f_r = fu * inv_dr;
+  const float f_t = fv * G.t_inv * tsel;
+  const float f_p = fw * G.p_inv;
+  const float A = f_r * inv_r;
+  const float ir2 = inv_r * inv_r;
+  const float B = f_t * z * ir2 * inv_rho;   // theta term, x and y components (per x, y)
+  const float C = f_p * inv_rho * inv_rho;   // phi term
+  const float D = f_t * rho * ir2;           // theta term, z component
+  s.gx = fmaf(A + B, x, -C * y);
+  s.gy = fmaf(A + B, y, C * x);
+  s.gz = fmaf(A, z, -D);
+  s.te = 0.f;
+  if (want_te) {
+    const float4 t0 = __ldg(G.te + 2 * cell);
+    const float4 t1 = __ldg(G.te + 2 * cell + 1);
+    const float p00 = fmaf(w, t0.y - t0.x, t0.x), p01 = fmaf(w, t0.w - t0.z, t0.z);
+    const float p10 = fmaf(w, t1.y - t1.x, t1.x), p11 = fmaf(w, t1.w - t1.z, t1.z);
+    const float q0 = fmaf(v, p01 - p00, p00), q1 = fmaf(v, p11 - p10, p10);
+    s.te = fmaf(u, q1 - q0, q0);
+  }
+  return s;
+}
+
+__device__ __forceinline__ Sample vacuum_sample() {
+  Sample s;
+  s.ne = 0.f; s.te = 0.f; s.gx = 0.f; s.gy = 0.f; s.gz = 0.f;
+  return s;
+}
+
+// radial cell of r from the lookup table: at most one node lies inside a bin
+__device__ __forceinline__ int radial_cell(const GridDev& G, float r) {
+  int bin = __float2int_rd((r - G.r_lut0) * G.r_lut_inv);
+  bin = min(max(bin, 0), G.r_lut_n - 1);
+  const int2 e = __ldg(G.r_lut + bin);
+  return min(e.x + (r >= __int_as_float(e.y) ? 1 : 0), G.n_r - 2);
+}
+
+__device__ __forceinline__ Sample eval_field(const GridDev& G, float x, float y, float z, bool want_te) {
   const float rho2 = fmaf(x, x, y * y);
   const float r2 = fmaf(z, z, rho2);
   const float inv_r = rsqrtf(r2);
   const float r = r2 * inv_r;
-  if (!(r <= G.r_vac)) {  // vacuum beyond the outer band (and NaN positions)
-    s.ne = 0.f; s.te = 0.f; s.gx = 0.f; s.gy = 0.f; s.gz = 0.f;
-    return s;
-  }
-  // radial cell from the lookup table: at most one node lies inside a bin
-  int bin = __float2int_rd((r - G.r_lut0) * G.r_lut_inv);
-  bin = min(max(bin, 0), G.r_lut_n - 1);
-  const int2 e = __ldg(G.r_lut + bin);
-  const int i = min(e.x + (r >= __int_as_float(e.y) ? 1 : 0), G.n_r - 2);
+  if (!(r <= G.r_vac)) return vacuum_sample();  // beyond the outer band (and NaN positions)
+  const int i = radial_cell(G, r);
   const float2 rc = __ldg(G.r_cell + i);
   const float u = (r - rc.x) * rc.y;
 
@@ -103,42 +153,126 @@ __device__ __forceinline__ Sample eval_field(const GridDev& G, float x, float y,
   const float pp = ph * G.p_inv;
   const int k = min(max(__float2int_rd(pp), 0), G.n_p - 1);
   const float w = pp - (float)k;
+  return sample_cell(G, i, j, k, u, v, w, tsel, rc.y, x, y, z, inv_r, rho, inv_rho, want_te);
+}
 
-  const int cell = (i * (G.n_t - 1) + j) * G.n_p + k;
-  const float4 c0 = __ldg(G.ne + 2 * cell);      // (000, 001, 010, 011)
-  const float4 c1 = __ldg(G.ne + 2 * cell + 1);  // (100, 101, 110, 111)
-  const float d00 = c0.y - c0.x, d01 = c0.w - c0.z, d10 = c1.y - c1.x, d11 = c1.w - c1.z;
-  const float a00 = fmaf(w, d00, c0.x), a01 = fmaf(w, d01, c0.z);
-  const float a10 = fmaf(w, d10, c1.x), a11 = fmaf(w, d11, c1.z);
-  const float e0 = a01 - a00, e1 = a11 - a10;
-  const float b0 = fmaf(v, e0, a00), b1 = fmaf(v, e1, a10);
-  const float fu = b1 - b0;
-  s.ne = fmaf(u, fu, b0);
-  const float fv = fmaf(u, e1 - e0, e0);
-  const float g0 = fmaf(v, d01 - d00, d00), g1 = fmaf(v, d11 - d10, d10);
-  const float fw = fmaf(u, g1 - g0, g0);
-
-  const float f_r = fu * rc.y;
-  const float f_t = fv * G.t_inv * tsel;
-  const float f_p = fw * G.p_inv;
-  const float A = f_r * inv_r;
-  const float ir2 = inv_r * inv_r;
-  const float B = f_t * z * ir2 * inv_rho;   // theta term, x and y components (per x, y)
-  const float C = f_p * inv_rho * inv_rho;   // phi term
-  const float D = f_t * rho * ir2;           // theta term, z component
-  s.gx = fmaf(A + B, x, -C * y);
-  s.gy = fmaf(A + B, y, C * x);
-  s.gz = fmaf(A, z, -D);
-  s.te = 0.f;
-  if (want_te) {
-    const float4 t0 = __ldg(G.te + 2 * cell);
-    const float4 t1 = __ldg(G.te + 2 * cell + 1);
-    const float p00 = fmaf(w, t0.y - t0.x, t0.x), p01 = fmaf(w, t0.w - t0.z, t0.z);
-    const float p10 = fmaf(w, t1.y - t1.x, t1.x), p11 = fmaf(w, t1.w - t1.z, t1.z);
-    const float q0 = fmaf(v, p01 - p00, p00), q1 = fmaf(v, p11 - p10, p10);
-    s.te = fmaf(u, q1 - q0, q0);
+// atan(num / den) with relative accuracy for small angles: the Taylor series
+// through q^13 for den > 0 and |q| = |num / den| <= 1/4 (truncation below
+// 3e-10 relative), else atan2_grid.
+__device__ __forceinline__ float atan_ratio(float num, float den) {
+  if (den > 0.f && fabsf(num) <= 0.25f * den) {
+    const float q = num / den;
+    const float t = q * q;
+    float p = 1.f / 13.f;
+    p = fmaf(p, t, -1.f / 11.f);
+    p = fmaf(p, t, 1.f / 9.f);
+    p = fmaf(p, t, -1.f / 7.f);
+    p = fmaf(p, t, 1.f / 5.f);
+    p = fmaf(p, t, -1.f / 3.f);
+    return fmaf(q * t, p, q);
   }
-  return s;
+  return atan2_grid(num, den);
+}
+
+// Evaluation about a base point.  A tube's neighbour ray sits ~1e-3 R_sun
+// from its central ray and the stage points of one RK4 step lie within
+// h |k| of its node; the tube needs the field's differences over such
+// offsets.  Evaluated at the rounded FP32 sum of base and offset, a point
+// moves by up to an ulp of |x| (~2e-7 R_sun), 1e-4 of a 1e-3 offset at
+// every evaluation, and one that lands within that distance of a cell face
+// takes the wrong cell's gradient (a kink jump as large as the whole
+// offset difference).  So the base point's (r, theta, phi) are formed once
+// per step, exactly as eval_field forms them, and each evaluation forms
+// the offsets of r, theta, phi from o without cancellation
+// (dr = (2 c.o + o.o) / (r + r_c), dtheta and dphi as the angles between
+// c and c + o) and adds them only inside the cell fractions, which then
+// keep FP32 precision relative to the cell; the cell is re-chosen from
+// those fractions.
+struct BasePoint {
+  float x, y, z;
+  float r, rho;    // |c|, its distance from the z axis
+  float tt, pp;    // theta and phi in cell units
+};
+
+__device__ __forceinline__ BasePoint base_point(const GridDev& G, float x, float y, float z) {
+  BasePoint c;
+  c.x = x; c.y = y; c.z = z;
+  const float rho2 = fmaf(x, x, y * y);
+  const float r2 = fmaf(z, z, rho2);
+  c.r = r2 * rsqrtf(r2);
+  c.rho = rho2 * ((rho2 > 0.f) ? rsqrtf(rho2) : 0.f);
+  c.tt = (atan2_grid(c.rho, z) - G.t0) * G.t_inv;
+  float ph = atan2_grid(y, x) - G.p0;
+  if (ph < 0.f) ph += kTwoPiF;
+  if (ph >= kTwoPiF) ph -= kTwoPiF;
+  c.pp = ph * G.p_inv;
+  return c;
+}
+
+__device__ __forceinline__ Sample eval_field_off(const GridDev& G, const BasePoint& c, float ox, float oy,
+                                                 float oz, bool want_te) {
+  const float x = c.x + ox, y = c.y + oy, z = c.z + oz;
+  const float rho2 = fmaf(x, x, y * y);
+  const float r2 = fmaf(z, z, rho2);
+  const float inv_r = rsqrtf(r2);
+  const float r = r2 * inv_r;
+  if (!(r <= G.r_vac)) return vacuum_sample();
+  const float inv_rho = (rho2 > 0.f) ? rsqrtf(rho2) : 0.f;
+  const float rho = rho2 * inv_rho;
+  // coordinate offsets
+  const float cxy = fmaf(c.x, ox, c.y * oy);
+  const float oxy = fmaf(ox, ox, oy * oy);
+  const float sr = r + c.r, srho = rho + c.rho;
+  const float dr = (sr > 0.f) ? fmaf(2.f, fmaf(c.z, oz, cxy), fmaf(oz, oz, oxy)) / sr : 0.f;
+  const float drho = (srho > 0.f) ? fmaf(2.f, cxy, oxy) / srho : 0.f;
+  const float dtt = atan_ratio(fmaf(c.z, drho, -c.rho * oz), fmaf(z, c.z, rho * c.rho)) * G.t_inv;
+  const float dpp = atan_ratio(fmaf(c.x, oy, -c.y * ox), fmaf(c.x, x, c.y * y)) * G.p_inv;
+
+  int i = radial_cell(G, r);
+  float2 rcell = __ldg(G.r_cell + i);
+  float u = ((c.r - rcell.x) + dr) * rcell.y;
+  if (u < 0.f && i > 0) {
+    --i;
+    rcell = __ldg(G.r_cell + i);
+    u = ((c.r - rcell.x) + dr) * rcell.y;
+  } else if (u >= 1.f && i < G.n_r - 2) {
+    ++i;
+    rcell = __ldg(G.r_cell + i);
+    u = ((c.r - rcell.x) + dr) * rcell.y;
+  }
+
+  const float tt = c.tt + dtt;
+  int j;
+  float v, tsel;
+  if (tt > 0.f && tt < G.t_last) {
+    j = min(__float2int_rd(tt), G.n_t - 2);
+    v = (c.tt - (float)j) + dtt;
+    if (v < 0.f && j > 0) {
+      --j;
+      v = (c.tt - (float)j) + dtt;
+    } else if (v >= 1.f && j < G.n_t - 2) {
+      ++j;
+      v = (c.tt - (float)j) + dtt;
+    }
+    tsel = 1.f;
+  } else if (tt <= 0.f) {
+    j = 0; v = 0.f; tsel = 0.f;
+  } else {
+    j = G.n_t - 2; v = 1.f; tsel = 0.f;
+  }
+  int k = __float2int_rd(c.pp + dpp);
+  float w = (c.pp - (float)k) + dpp;
+  if (w < 0.f) {
+    --k;
+    w = (c.pp - (float)k) + dpp;
+  } else if (w >= 1.f) {
+    ++k;
+    w = (c.pp - (float)k) + dpp;
+  }
+  if (k < 0) k += G.n_p;  // periodic in phi
+  else if (k >= G.n_p) k -= G.n_p;
+  k = min(max(k, 0), G.n_p - 1);
+  return sample_cell(G, i, j, k, u, v, w, tsel, rcell.y, x, y, z, inv_r, rho, inv_rho, want_te);
 }
 
 // ------------------------------------------------------------------- RK4
@@ -177,6 +311,47 @@ __device__ __forceinline__ Rk4Out rk4_step(const GridDev& G, float kf, float h, 
   o.Ax = fmaf(2.f, ax, o.Ax); o.Ay = fmaf(2.f, ay, o.Ay); o.Az = fmaf(2.f, az, o.Az);
   // stage 4
   s = eval_field(G, fmaf(h, q3x, px), fmaf(h, q3y, py), fmaf(h, q3z, pz), false);
+  o.Ax = fmaf(kf, s.gx, o.Ax); o.Ay = fmaf(kf, s.gy, o.Ay); o.Az = fmaf(kf, s.gz, o.Az);
+  return o;
+}
+
+// One RK4 step of a ray of a tube bundle about the base point b, the
+// FP32 node position of the bundle's central ray: the central ray is at
+// b + l (l: the low part of its compensated position, 0 in plain FP32)
+// with wave vector k, and this lane's ray at offsets (dp, dk) from it (0 on
+// the central lane).  Every stage point is b plus an offset that holds
+// l, the stage's displacement along k and the lane's own offsets, so each
+// evaluation (eval_field_off) resolves it to FP32 precision of the offset.
+// Outputs as rk4_step.
+__device__ __forceinline__ Rk4Out rk4_step_base(const GridDev& G, float kf, float h, const BasePoint& b,
+                                                float lx, float ly, float lz, float kx, float ky, float kz,
+                                                float dpx, float dpy, float dpz, float dkx, float dky,
+                                                float dkz, bool want_te) {
+  Rk4Out o;
+  const float hh = 0.5f * h;
+  // stage 1 at b + l + dp
+  Sample s = eval_field_off(G, b, lx + dpx, ly + dpy, lz + dpz, want_te);
+  o.ne1 = s.ne;
+  o.te1 = s.te;
+  float ax = kf * s.gx, ay = kf * s.gy, az = kf * s.gz;
+  o.Gx = ax; o.Gy = ay; o.Gz = az;
+  o.Ax = ax; o.Ay = ay; o.Az = az;
+  // stages 2 and 3 at b + (l + hh k) + dp + hh (dk [+ hh a1])
+  const float mx = fmaf(hh, kx, lx), my = fmaf(hh, ky, ly), mz = fmaf(hh, kz, lz);
+  const float s3x = fmaf(hh, fmaf(hh, ax, dkx), dpx), s3y = fmaf(hh, fmaf(hh, ay, dky), dpy),
+              s3z = fmaf(hh, fmaf(hh, az, dkz), dpz);
+  s = eval_field_off(G, b, mx + fmaf(hh, dkx, dpx), my + fmaf(hh, dky, dpy), mz + fmaf(hh, dkz, dpz), false);
+  ax = kf * s.gx; ay = kf * s.gy; az = kf * s.gz;
+  o.Gx += ax; o.Gy += ay; o.Gz += az;
+  o.Ax = fmaf(2.f, ax, o.Ax); o.Ay = fmaf(2.f, ay, o.Ay); o.Az = fmaf(2.f, az, o.Az);
+  // stage 4 at b + (l + h k) + dp + h (dk + hh a2)
+  const float s4x = fmaf(h, fmaf(hh, ax, dkx), dpx), s4y = fmaf(h, fmaf(hh, ay, dky), dpy),
+              s4z = fmaf(h, fmaf(hh, az, dkz), dpz);
+  s = eval_field_off(G, b, mx + s3x, my + s3y, mz + s3z, false);
+  ax = kf * s.gx; ay = kf * s.gy; az = kf * s.gz;
+  o.Gx += ax; o.Gy += ay; o.Gz += az;
+  o.Ax = fmaf(2.f, ax, o.Ax); o.Ay = fmaf(2.f, ay, o.Ay); o.Az = fmaf(2.f, az, o.Az);
+  s = eval_field_off(G, b, fmaf(h, kx, lx) + s4x, fmaf(h, ky, ly) + s4y, fmaf(h, kz, lz) + s4z, false);
   o.Ax = fmaf(kf, s.gx, o.Ax); o.Ay = fmaf(kf, s.gy, o.Ay); o.Az = fmaf(kf, s.gz, o.Az);
   return o;
 }
@@ -266,7 +441,9 @@ enum RayStatus { kExitOuter = 1, kHitInner = 2, kTauStop = 3, kStepLimit = 4, kM
 struct ViewDev {
   float ox, oy, oz, eux, euy, euz, evx, evy, evz;
   float x0, dx, y0, dy;
-  int nx, npix;
+  int nx, ny, npix;
+  int tile, tiles_x;   // image mode: tickets walk tile x tile pixel blocks (0: rows)
+  int tickets;         // tickets per frequency (npix, or padded to whole tiles)
 };
 
 // Batched work: one map = (request, frequency) with its output slab; one
@@ -305,6 +482,8 @@ struct TraceParams {
   float tbc_K;
   int emission;
   int straight;
+  int blocks_per_sm;                 // persistent blocks per SM (0: as many as fit)
+  float tube_delta, inv_delta2;      // tube mode: image-plane offset and 1 / delta^2
   // image mode: one view, nf frequencies, ticket t -> (frequency t / npix, pixel t mod npix)
   ViewDev view;
   int nf;

@@ -9,12 +9,15 @@ Bars.
     interpolant is chaotic where stage points fall within rounding distance
     of a cell face (the interpolant's gradient jumps there).  The oracle
     measures each ray's own single-precision conditioning by re-tracing it
-    with r, theta, phi perturbed at the 1e-6 level (three seeds; the GPU's
-    single-precision geometry errs by ~3e-7); a ray must
-    match within max(strict bar, 10 x its spread), with the same status
+    with r, theta, phi perturbed at the 1e-6 level (six seeds; the GPU's
+    single-precision geometry errs by ~3e-7: a face flip is a rare event per
+    stage point, so a single seed finds one only now and then); a ray must
+    match within max(strict bar, 10 x its spread) in T_b, exit and ln S,
+    with the same status
     unless the status itself flips under the perturbation, and at least 60%
     of the rays must be well-conditioned in T_b (spread below a tenth of the
-    T_b bar) so that the bounds are not vacuous.
+    T_b bar) so that the bounds are not vacuous (30% in tube mode, whose
+    persistent neighbours are intrinsically worse conditioned: TUBE_MIN_WELL).
   ln S (compensated form): 1e-3 absolute.  Near a turning point n -> 0, so
     eps = eta |dr| -> 0 (Eq. 8) and FP32 neighbour geometry resolves the
     pair separation only to ulp(r) / eps.
@@ -79,23 +82,26 @@ def run_oracle(orc, g, v, freqs, pixels=None, **opt):
 
 
 def spreads(orc, g, v, freqs, ref, pixels=None, **opt):
-    """Per-ray single-precision conditioning of the oracle (T_b, exit, status flips)."""
+    """Per-ray single-precision conditioning of the oracle (T_b, exit, ln S, status flips)."""
     stb = np.zeros_like(ref["tb"])
     sex = np.zeros(ref["tb"].shape)
+    sls = np.zeros(ref["tb"].shape)
     flip = np.zeros(ref["tb"].shape, bool)
-    for seed in (1, 2, 3):
+    for seed in range(1, 7):
         j = run_oracle(orc, g, v, freqs, pixels=pixels, jitter=JITTER, jitter_seed=seed, **dict(opt))
         stb = np.maximum(stb, np.abs(j["tb"] - ref["tb"]))
         sex = np.maximum(sex, np.linalg.norm(j["exit"] - ref["exit"], axis=-1))
+        sls = np.maximum(sls, np.abs(j["ln_s"] - ref["ln_s"]))
         flip |= j["status"] != ref["status"]
-    return stb, sex, flip
+    return stb, sex, sls, flip
 
 
 def _scale(ref_tb):
     return np.maximum(ref_tb, np.maximum(1e-2 * ref_tb.max(axis=1, keepdims=True), 1e-30))
 
 
-def compare(gpu, ref, pixels=None, tb_rel=TB_REL, exit_abs=EXIT_ABS, lns_abs=None, cond=None, label=""):
+def compare(gpu, ref, pixels=None, tb_rel=TB_REL, exit_abs=EXIT_ABS, lns_abs=None, cond=None, label="",
+            min_well=0.6):
     sel = (lambda a: a) if pixels is None else (lambda a: a[:, pixels])
     g_tb, g_st, g_ex, g_ls = sel(gpu["tb"]), sel(gpu["status"]), sel(gpu["exit"]), sel(gpu["ln_s"])
     scale = _scale(ref["tb"])
@@ -107,7 +113,7 @@ def compare(gpu, ref, pixels=None, tb_rel=TB_REL, exit_abs=EXIT_ABS, lns_abs=Non
         tb_bound = tb_rel * scale
         ex_bound = np.full(dex.shape, exit_abs)
     else:
-        stb, sex, flip = cond
+        stb, sex, sls, flip = cond
         well = ~flip
         tb_bound = np.maximum(tb_rel * scale, 10 * stb)
         ex_bound = np.maximum(exit_abs, 10 * sex)
@@ -127,12 +133,16 @@ def compare(gpu, ref, pixels=None, tb_rel=TB_REL, exit_abs=EXIT_ABS, lns_abs=Non
             det = [(i, dex[i], ex_bound[i], cond[1][i] if cond else None, ref["status"][i]) for i in idx]
             raise AssertionError(f"{label}: exit error (idx, err, bound, spread, status) {det}")
     if lns_abs is not None:
-        dl = np.abs(g_ls - ref["ln_s"])[well]
-        assert dl.max() <= lns_abs, f"{label}: ln S error {dl.max():.3e}"
+        ls_bound = np.full(dex.shape, lns_abs) if cond is None else np.maximum(lns_abs, 10 * cond[2])
+        bad_ls = well & (np.abs(g_ls - ref["ln_s"]) > ls_bound)
+        if bad_ls.any():
+            idx = [tuple(i) for i in np.argwhere(bad_ls)[:4]]
+            det = [(i, g_ls[i], ref["ln_s"][i], ls_bound[i]) for i in idx]
+            raise AssertionError(f"{label}: ln S out of bounds (idx, gpu, oracle, bound) {det}")
     if cond is not None:
         # the per-ray bounds must not be vacuous: most rays are well-conditioned
         frac = (cond[0] <= 0.1 * tb_rel * scale).mean()
-        assert frac >= 0.6, f"{label}: only {frac:.0%} of rays well-conditioned in T_b"
+        assert frac >= min_well, f"{label}: only {frac:.0%} of rays well-conditioned in T_b"
     return {"max_tb_rel": float((dtb / scale).max()), "max_exit": float(dex[ends].max()) if ends.any() else 0.0,
             "no_flip": float(well.mean())}
 
@@ -211,10 +221,11 @@ def test_tiny_other_frequencies(rt, ctx, orc, tiny, freq):
     compare(gpu, ref, lns_abs=1e-3, label=f"tiny {freq / 1e6:.0f} MHz")
 
 
-@pytest.mark.parametrize("n_nb,s_mode", [(2, 0), (4, 0), (8, 0), (4, 2)])
+@pytest.mark.parametrize("n_nb,s_mode", [(2, 0), (4, 0), (8, 0), (4, 2), (2, 1), (4, 1), (8, 1)])
 def test_neighbour_counts_and_modes(rt, ctx, orc, n_nb, s_mode):
-    """2 (paper), 4 and 8 neighbours and magnification off, on a smooth
-    non-symmetric corona seen from an off-axis observer."""
+    """Step-wise with 2 (paper), 4 and 8 neighbours, magnification off, and
+    tube mode with 2, 4, 8 persistent neighbours, on a smooth non-symmetric
+    corona seen from an off-axis observer."""
     g = smooth_grid()
     v = cs.View(0.7, 0.3, 13, 7, -2.2, 2.6, -1.9, 2.1)
     freqs = [45e6, 150e6, 700e6]
@@ -222,7 +233,34 @@ def test_neighbour_counts_and_modes(rt, ctx, orc, n_nb, s_mode):
     gpu = run_gpu(rt, ctx, grid, v, freqs, n_nb=n_nb, s_mode=s_mode, precision=1)
     ref = run_oracle(orc, g, v, freqs, n_nb=n_nb, s_mode=s_mode)
     cond = spreads(orc, g, v, freqs, ref, n_nb=n_nb, s_mode=s_mode)
-    compare(gpu, ref, cond=cond, lns_abs=1e-3 if s_mode == 0 else 0.0, label=f"nb{n_nb} mode{s_mode}")
+    compare(gpu, ref, cond=cond, lns_abs=0.0 if s_mode == 2 else 1e-3, label=f"nb{n_nb} mode{s_mode}",
+            min_well=TUBE_MIN_WELL if s_mode == 1 else 0.6)
+
+
+# Tube mode (persistent neighbours) on the trilinear interpolant is far less
+# well-conditioned than the step-wise retrace: a neighbour's RK4 stage point
+# that crosses a cell face one step earlier or later than in the reference
+# changes its acceleration by the face's kink, a jump as large as the whole
+# offset difference, and the tube carries it to the end of the path.
+# Measured with the oracle's own 1e-6 perturbation on this view, 35-63% of
+# the tube rays (any of 64 to 1024 radial nodes) against 100% of the
+# step-wise rays stay within a tenth of the T_b bar; the per-ray bounds stay,
+# the non-vacuity floor for tube mode is 30%.
+TUBE_MIN_WELL = 0.3
+
+
+@pytest.mark.parametrize("n_nb", [2, 4, 8])
+def test_tube_mode_symmetric(rt, ctx, orc, tiny, n_nb):
+    """Tube mode on the spherically symmetric corona, per-ray conditioned bars."""
+    g, _, _ = tiny
+    v = cs.View(0.0, 0.0, 17, 15, -2.4, 2.4, -2.2, 2.5)
+    freqs = [70e6, 250e6]
+    grid = ctx.load(g)
+    gpu = run_gpu(rt, ctx, grid, v, freqs, s_mode=1, n_nb=n_nb, precision=1)
+    ref = run_oracle(orc, g, v, freqs, s_mode=1, n_nb=n_nb)
+    cond = spreads(orc, g, v, freqs, ref, s_mode=1, n_nb=n_nb)
+    compare(gpu, ref, cond=cond, lns_abs=1e-3, label=f"tube nb{n_nb}", min_well=TUBE_MIN_WELL)
+    assert np.abs(ref["ln_s"]).max() > 1e-3  # the tube does change
 
 
 def test_rough_corona_conditioned(rt, ctx, orc, tiny):
