@@ -29,25 +29,13 @@ __device__ __forceinline__ Dl operator-(Dl a, Dl b) { return {a.v - b.v, a.d - b
 __device__ __forceinline__ Dl operator*(Dl a, Dl b) { return {a.v * b.v, fmaf(a.d, b.v, a.v * b.d)}; }
 __device__ __forceinline__ Dl operator*(float s, Dl a) { return {s * a.v, s * a.d}; }
 __device__ __forceinline__ Dl operator-(Dl a) { return {-a.v, -a.d}; }
-__device__ __forceinline__ Dl recip(Dl a) {
-  const float r = 1.f / a.v;
-  return {r, -a.d * r * r};
-}
-__device__ __forceinline__ Dl dsqrt(Dl a) {
-  const float s = sqrtf(a.v);
-  return {s, s > 0.f ? 0.5f * a.d / s : 0.f};
-}
-// atan2 with the forward's polynomial for the value; exact derivative.
-__device__ __forceinline__ Dl datan2(Dl y, Dl x) {
-  const float q = x.v * x.v + y.v * y.v;
-  return {atan2_grid(y.v, x.v), q > 0.f ? (x.v * y.d - y.v * x.d) / q : 0.f};
-}
 
 // --------------------------------------------------------- cell geometry
 struct CellGeom {
   int i, j, k, k1;           // cell and wrapped phi neighbour
   float u, v, w, tsel;       // fractions; tsel = 0 in the clamped theta caps
   Vec du, dv, dw;            // Cartesian gradients of u, v, w
+  float inv_r, rho, inv_rho; // 1 / |x|, distance from the z axis and its inverse (0 on the axis)
   bool vac;                  // beyond the outer band
 };
 
@@ -62,6 +50,7 @@ __device__ __forceinline__ CellGeom cell_geom(const GridDev& G, float x, float y
     c.i = c.j = c.k = c.k1 = 0;
     c.u = c.v = c.w = c.tsel = 0.f;
     c.du = c.dv = c.dw = {0.f, 0.f, 0.f};
+    c.inv_r = c.rho = c.inv_rho = 0.f;
     return c;
   }
   int bin = __float2int_rd((r - G.r_lut0) * G.r_lut_inv);
@@ -72,6 +61,9 @@ __device__ __forceinline__ CellGeom cell_geom(const GridDev& G, float x, float y
   c.u = (r - rc.x) * rc.y;
   const float inv_rho = (rho2 > 0.f) ? rsqrtf(rho2) : 0.f;
   const float rho = rho2 * inv_rho;
+  c.inv_r = inv_r;
+  c.rho = rho;
+  c.inv_rho = inv_rho;
   const float tt = (atan2_grid(rho, z) - G.t0) * G.t_inv;
   if (tt > 0.f && tt < G.t_last) {
     c.j = min(__float2int_rd(tt), G.n_t - 2);
@@ -160,29 +152,26 @@ __device__ __forceinline__ Vec force_adjoint(const GridDev& G, float kf, float x
         const float coef = sg[a] * wv[b] * ww[cc] * gu + wu[a] * sg[b] * ww[cc] * gv + wu[a] * wv[b] * sg[cc] * gw;
         atomicAdd(dne + node_index(G, c, a, b, cc), kf * coef);
       }
-  // Hessian-vector product: tangent of grad n_e along lam
+  // Hessian-vector product: tangent of grad n_e along lam.  The tangents of
+  // the fractions are lam . grad (u, v, w) = (gu, gv, gw); those of r, rho
+  // follow from x . lam.
   const Dl X{x, lam.x}, Y{y, lam.y}, Z{z, lam.z};
-  const Dl rho2 = X * X + Y * Y;
-  const Dl r2 = rho2 + Z * Z;
-  const Dl r = dsqrt(r2);
-  const Dl inv_r = recip(r);
+  const float rho_d = (x * lam.x + y * lam.y) * c.inv_rho;
+  const float r_d = fmaf(z, lam.z, x * lam.x + y * lam.y) * c.inv_r;
+  const Dl inv_r{c.inv_r, -r_d * c.inv_r * c.inv_r};
+  const Dl rho{c.rho, rho_d};
+  const Dl inv_rho{c.inv_rho, -rho_d * c.inv_rho * c.inv_rho};
   const float2 rc = __ldg(G.r_cell + c.i);
-  const Dl u = rc.y * (r - dl(rc.x));
-  const Dl rho = dsqrt(rho2);
-  const Dl inv_rho = (rho.v > 0.f) ? recip(rho) : dl(0.f);
-  Dl v = dl(c.v);
-  if (c.tsel > 0.f) v = G.t_inv * (datan2(rho, Z) - dl(G.t0)) - dl((float)c.j);
-  const Dl w = G.p_inv * datan2(Y, X) - dl(c.w + (float)c.k) + dl(c.w);  // only the tangent of w matters
   const int cell = (c.i * (G.n_t - 1) + c.j) * G.n_p + c.k;
   const float4 c0 = __ldg(G.ne + 2 * cell), c1 = __ldg(G.ne + 2 * cell + 1);
   const float d00 = c0.y - c0.x, d01 = c0.w - c0.z, d10 = c1.y - c1.x, d11 = c1.w - c1.z;
-  const Dl W{c.w, w.d};
+  const Dl W{c.w, gw};
   const Dl a00 = dl(c0.x) + d00 * W, a01 = dl(c0.z) + d01 * W;
   const Dl a10 = dl(c1.x) + d10 * W, a11 = dl(c1.z) + d11 * W;
   const Dl e0 = a01 - a00, e1 = a11 - a10;
-  const Dl V{c.v, v.d};
+  const Dl V{c.v, gv};
   const Dl b0 = a00 + V * e0, b1 = a10 + V * e1;
-  const Dl U{c.u, u.d};
+  const Dl U{c.u, gu};
   const Dl fu = b1 - b0;
   const Dl fv = e0 + U * (e1 - e0);
   const Dl g0 = dl(d00) + (d01 - d00) * V, g1 = dl(d10) + (d11 - d10) * V;
@@ -303,12 +292,24 @@ struct AdjState {
   float Wsuf;
   float lr[3], lk[3];          // adjoint of the node state at the end of the step being reversed
   float lkap, lte;             // partial adjoints of kappa and T_e at that node
-  float lt[3], le1[3], le2[3], leps, lalpha;  // tube-area adjoints between the sub-steps
-  float lpc[3];
+  // per-step adjoints handed from the transfer/tube part (A) and the
+  // neighbours (B) of step m to the central reverse (C) of the same step one
+  // iteration later; double-buffered by the parity of m
+  struct {
+    float lt[3], le1[3], le2[3], leps, lalpha;  // chord, basis and eps adjoints
+    float lpc[3];                                // the clip point (clipped last step)
+    float slp[3], slk[3];                        // sum of the neighbour seed adjoints
+  } st[2];
+  float lpos[3];               // value adjoint of the node A just completed
 };
 
+#ifndef RT_ADJ_MIN_BLOCKS
+#define RT_ADJ_MIN_BLOCKS 5
+#endif
+constexpr int kAdjMinBlocks = RT_ADJ_MIN_BLOCKS;  // occupancy target: 5 x 128 threads per SM
+
 template <int NB>
-__global__ void __launch_bounds__(kThreads) adjoint_bundles(const __grid_constant__ AdjParams P) {
+__global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_bundles(const __grid_constant__ AdjParams P) {
   constexpr int L = NB + 1;
   constexpr int BPW = 32 / L;
   constexpr int K = kCkptEvery;
@@ -370,12 +371,18 @@ __global__ void __launch_bounds__(kThreads) adjoint_bundles(const __grid_constan
     if (!__any_sync(kFull, active)) break;
 
     // ---------------------------------------------- recompute the segment
+    // Pipelined as the forward: in iteration j the central lane steps node
+    // m0 + j while its neighbours retrace step m0 + j - 1 from the seeds
+    // broadcast one iteration earlier, all in one RK4 pass.
     const int m0 = active ? A.seg * K : 0;
     const int n_s = active ? min(K, A.N - m0) : 0;
     const bool last_seg = active && (m0 + n_s == A.N);
+    const int ns_b = __shfl_sync(kFull, n_s, base);      // the bundle's segment length, on every lane
+    const int ns_w = __reduce_max_sync(kFull, ns_b);     // the warp's longest
     float px = 0.f, py = 0.f, pz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
     float rlx = 0.f, rly = 0.f, rlz = 0.f, klx = 0.f, kly = 0.f, klz = 0.f;
     float tau = 0.f, lns = 0.f;
+    bool has_seed = false;  // neighbour lanes: a retrace is pending
     if (central && active) {
       const Ckpt& c = P.ckpt[P.ck_off[item] + A.seg];
       px = c.r[0]; py = c.r[1]; pz = c.r[2];
@@ -386,12 +393,37 @@ __global__ void __launch_bounds__(kThreads) adjoint_bundles(const __grid_constan
       lns = c.lns_hi + c.lns_lo;
     }
     const float kf_lane = __shfl_sync(kFull, (central && active) ? A.kf : 0.f, base);
-    for (int j = 0; j < K; ++j) {
-      // R1: the central step m0 + j
+    for (int j = 0; j <= ns_w; ++j) {
       const bool cw = central && j < n_s;
+      Rk4Out o;
+      o.Gx = o.Gy = o.Gz = o.Ax = o.Ay = o.Az = 0.f;
+      o.ne1 = o.te1 = 0.f;
+      if (cw || (NB > 0 && has_seed)) o = rk4_step(P.G, kf_lane, h, px, py, pz, kx, ky, kz, cw);
+      if (NB > 0) {
+        // separations of the retraced step m0 + j - 1: D_j = G_{+j} - G_{-j}
+        const float dx = o.Gx - __shfl_down_sync(kFull, o.Gx, 1);
+        const float dy = o.Gy - __shfl_down_sync(kFull, o.Gy, 1);
+        const float dz = o.Gz - __shfl_down_sync(kFull, o.Gz, 1);
+        const Vec d1{__shfl_sync(kFull, dx, base + 1), __shfl_sync(kFull, dy, base + 1), __shfl_sync(kFull, dz, base + 1)};
+        const Vec d2{__shfl_sync(kFull, dx, base + 3), __shfl_sync(kFull, dy, base + 3), __shfl_sync(kFull, dz, base + 3)};
+        if (central && j >= 1 && j - 1 < n_s) {
+          StepRec& rc = R[j - 1];
+          const float sc = P.h2_12 / rc.eps;
+          const Vec c1{sc * d1.x, sc * d1.y, sc * d1.z}, c2{sc * d2.x, sc * d2.y, sc * d2.z};
+          const Vec tp{rc.t[0], rc.t[1], rc.t[2]}, e1p{rc.e1[0], rc.e1[1], rc.e1[2]}, e2p{rc.e2[0], rc.e2[1], rc.e2[2]};
+          const float lm = ln_m(c1, c2, e1p, e2p, tp);
+          rc.c1[0] = c1.x; rc.c1[1] = c1.y; rc.c1[2] = c1.z;
+          rc.c2[0] = c2.x; rc.c2[1] = c2.y; rc.c2[2] = c2.z;
+          rc.lnm = lm;
+          lns += lm;
+          rc.lns_next = lns;
+        }
+      } else if (central && j >= 1 && j - 1 < n_s) {
+        R[j - 1].lnm = 0.f;
+        R[j - 1].lns_next = lns;
+      }
       Vec sr{0.f, 0.f, 0.f}, sk{0.f, 0.f, 0.f}, sa{0.f, 0.f, 0.f}, sb{0.f, 0.f, 0.f};
       if (cw) {
-        const Rk4Out o = rk4_step(P.G, A.kf, h, px, py, pz, kx, ky, kz, true);
         const float kap = P.emission ? kappa_vac(o.ne1, o.te1, A.kap_c, A.ln_f) : 0.f;
         if (j > 0) tau += 0.5f * (R[j - 1].kap + kap) * P.hrsun;
         StepRec& rc = R[j];
@@ -432,7 +464,7 @@ __global__ void __launch_bounds__(kThreads) adjoint_bundles(const __grid_constan
         kx = mx; ky = my; kz = mz;
       }
       if (NB > 0) {
-        // R2: the neighbours retrace step m0 + j from the broadcast seeds
+        // seeds of step m0 + j for the next iteration: +-eps e1 (roles 1, 2), +-eps e2 (3, 4)
         const bool e = __shfl_sync(kFull, cw ? 1 : 0, base) != 0;
         const float bx = __shfl_sync(kFull, sr.x, base), by = __shfl_sync(kFull, sr.y, base),
                     bz = __shfl_sync(kFull, sr.z, base);
@@ -442,33 +474,14 @@ __global__ void __launch_bounds__(kThreads) adjoint_bundles(const __grid_constan
                     az = __shfl_sync(kFull, sa.z, base);
         const float cx = __shfl_sync(kFull, sb.x, base), cy = __shfl_sync(kFull, sb.y, base),
                     cz = __shfl_sync(kFull, sb.z, base);
-        Rk4Out o;
-        o.Gx = o.Gy = o.Gz = 0.f;
-        if (used && q > 0 && e) {
+        if (used && q > 0) {
+          has_seed = e;
           const float sgn = (q & 1) ? 1.f : -1.f;
-          const float ox = sgn * ((q <= 2) ? ax : cx), oy = sgn * ((q <= 2) ? ay : cy), oz = sgn * ((q <= 2) ? az : cz);
-          o = rk4_step(P.G, kf_lane, h, bx + ox, by + oy, bz + oz, bkx, bky, bkz, false);
+          px = bx + sgn * ((q <= 2) ? ax : cx);
+          py = by + sgn * ((q <= 2) ? ay : cy);
+          pz = bz + sgn * ((q <= 2) ? az : cz);
+          kx = bkx; ky = bky; kz = bkz;
         }
-        const float dx = o.Gx - __shfl_down_sync(kFull, o.Gx, 1);
-        const float dy = o.Gy - __shfl_down_sync(kFull, o.Gy, 1);
-        const float dz = o.Gz - __shfl_down_sync(kFull, o.Gz, 1);
-        const Vec d1{__shfl_sync(kFull, dx, base + 1), __shfl_sync(kFull, dy, base + 1), __shfl_sync(kFull, dz, base + 1)};
-        const Vec d2{__shfl_sync(kFull, dx, base + 3), __shfl_sync(kFull, dy, base + 3), __shfl_sync(kFull, dz, base + 3)};
-        if (cw) {
-          StepRec& rc = R[j];
-          const float sc = P.h2_12 / rc.eps;
-          const Vec c1{sc * d1.x, sc * d1.y, sc * d1.z}, c2{sc * d2.x, sc * d2.y, sc * d2.z};
-          const Vec tp{rc.t[0], rc.t[1], rc.t[2]}, e1p{rc.e1[0], rc.e1[1], rc.e1[2]}, e2p{rc.e2[0], rc.e2[1], rc.e2[2]};
-          const float lm = ln_m(c1, c2, e1p, e2p, tp);
-          rc.c1[0] = c1.x; rc.c1[1] = c1.y; rc.c1[2] = c1.z;
-          rc.c2[0] = c2.x; rc.c2[1] = c2.y; rc.c2[2] = c2.z;
-          rc.lnm = lm;
-          lns += lm;
-          rc.lns_next = lns;
-        }
-      } else if (cw) {
-        R[j].lnm = 0.f;
-        R[j].lns_next = lns;
       }
     }
     // the closing node of the segment: node m0 + n_s (the clip point on a clipped final step)
@@ -500,14 +513,23 @@ __global__ void __launch_bounds__(kThreads) adjoint_bundles(const __grid_constan
     }
 
     // ------------------------------------------------ reverse the segment
-    for (int j = K - 1; j >= 0; --j) {
-      const bool cw = central && j < n_s;
-      const bool last_step = cw && last_seg && j == n_s - 1;
+    // Pipelined: in iteration t the central lane runs the transfer and
+    // tube-area adjoint of step m0 + t (A) and the reverse of its own RK4
+    // step m0 + t + 1 (C), while its neighbours reverse their retrace of step
+    // m0 + t (B); B and C share one rk4_reverse pass.  C of step t + 1 needs
+    // A and B of step t + 1, which the previous iteration left in the
+    // bundle's shared state.
+    for (int t = ns_w - 1; t >= -1; --t) {
+      const bool a_ok = central && t >= 0 && t < n_s;
+      const bool c_ok = central && t + 1 < n_s;
+      const bool b_ok = NB > 0 && used && q > 0 && t >= 0 && t < ns_b;
+      // A: transfer of segment m = m0 + t (Eq. 2 front to back, differentiated)
       float lD1x = 0.f, lD1y = 0.f, lD1z = 0.f, lD2x = 0.f, lD2y = 0.f, lD2z = 0.f;
-      if (cw) {
-        // A: transfer of segment m = m0 + j (Eq. 2 front to back, differentiated)
-        const StepRec& rc = R[j];
-        const StepRec& rn = R[j + 1];
+      if (a_ok) {
+        auto& S = A.st[t & 1];
+        const bool last_step = last_seg && t == n_s - 1;
+        const StepRec& rc = R[t];
+        const StepRec& rn = R[t + 1];
         const float alpha = (last_step && A.clipped) ? A.alpha : 1.f;
         const float kap_sum = rc.kap + rn.kap;
         const float dt = 0.5f * kap_sum * P.hrsun * alpha;
@@ -521,136 +543,160 @@ __global__ void __launch_bounds__(kThreads) adjoint_bundles(const __grid_constan
         const float lLnM = A.lamT * (W + A.Wsuf);
         A.Wsuf += W;
         const float lk_node = 0.5f * P.hrsun * alpha * lDt;
-        float lkap_n = A.lkap + lk_node;
-        float lte_n = A.lte + 0.5f * lTbar;
-        A.lalpha = 0.5f * kap_sum * P.hrsun * lDt;
+        const float lkap_n = A.lkap + lk_node;
+        const float lte_n = A.lte + 0.5f * lTbar;
+        S.lalpha = 0.5f * kap_sum * P.hrsun * lDt;
         // node m+1 is complete: scatter its value adjoints
         float dkn, dkt;
         kappa_partials(rn.ne, rn.te, A.kap_c, A.ln_f, dkn, dkt);
         if (!P.emission) { dkn = 0.f; dkt = 0.f; }
-        const Vec lpos = value_adjoint(P.G, rn.r[0], rn.r[1], rn.r[2], lkap_n * dkn, lte_n + lkap_n * dkt, P.dne, P.dte);
+        const Vec lpos = value_adjoint(P.G, rn.r[0], rn.r[1], rn.r[2], lkap_n * dkn, lte_n + lkap_n * dkt,
+                                       P.dne, P.dte);
         if (last_step && A.clipped) {
-          A.lpc[0] = lpos.x; A.lpc[1] = lpos.y; A.lpc[2] = lpos.z;
+          S.lpc[0] = lpos.x; S.lpc[1] = lpos.y; S.lpc[2] = lpos.z;
+          A.lpos[0] = A.lpos[1] = A.lpos[2] = 0.f;
         } else {
-          A.lr[0] += lpos.x; A.lr[1] += lpos.y; A.lr[2] += lpos.z;
+          A.lpos[0] = lpos.x; A.lpos[1] = lpos.y; A.lpos[2] = lpos.z;
         }
         A.lkap = lk_node;  // node m, completed by segment m - 1
         A.lte = 0.5f * lTbar;
-        // tube area of step m (Eqs. 9-11, differentiated)
-        A.lt[0] = A.lt[1] = A.lt[2] = 0.f;
-        A.le1[0] = A.le1[1] = A.le1[2] = 0.f;
-        A.le2[0] = A.le2[1] = A.le2[2] = 0.f;
-        A.leps = 0.f;
+        // tube area of step m (Eqs. 9-11, differentiated); the neighbour
+        // seeds add their parts after B
+        S.lt[0] = S.lt[1] = S.lt[2] = 0.f;
+        S.le1[0] = S.le1[1] = S.le1[2] = 0.f;
+        S.le2[0] = S.le2[1] = S.le2[2] = 0.f;
+        S.leps = 0.f;
+        S.slp[0] = S.slp[1] = S.slp[2] = S.slk[0] = S.slk[1] = S.slk[2] = 0.f;
         if (NB > 0) {
           const Vec c1{rc.c1[0], rc.c1[1], rc.c1[2]}, c2{rc.c2[0], rc.c2[1], rc.c2[2]};
-          const Vec t{rc.t[0], rc.t[1], rc.t[2]}, e1{rc.e1[0], rc.e1[1], rc.e1[2]}, e2{rc.e2[0], rc.e2[1], rc.e2[2]};
+          const Vec t3{rc.t[0], rc.t[1], rc.t[2]}, e1{rc.e1[0], rc.e1[1], rc.e1[2]}, e2{rc.e2[0], rc.e2[1], rc.e2[2]};
           const float lm1 = lLnM * __expf(-rc.lnm);  // d ln(1 + m1) / d m1 = 1 / M
-          const Vec c2xt{c2.y * t.z - c2.z * t.y, c2.z * t.x - c2.x * t.z, c2.x * t.y - c2.y * t.x};
-          const Vec txc1{t.y * c1.z - t.z * c1.y, t.z * c1.x - t.x * c1.z, t.x * c1.y - t.y * c1.x};
+          const Vec c2xt{c2.y * t3.z - c2.z * t3.y, c2.z * t3.x - c2.x * t3.z, c2.x * t3.y - c2.y * t3.x};
+          const Vec txc1{t3.y * c1.z - t3.z * c1.y, t3.z * c1.x - t3.x * c1.z, t3.x * c1.y - t3.y * c1.x};
           const Vec lc1{lm1 * (e1.x + c2xt.x), lm1 * (e1.y + c2xt.y), lm1 * (e1.z + c2xt.z)};
           const Vec lc2{lm1 * (e2.x + txc1.x), lm1 * (e2.y + txc1.y), lm1 * (e2.z + txc1.z)};
-          A.le1[0] = lm1 * c1.x; A.le1[1] = lm1 * c1.y; A.le1[2] = lm1 * c1.z;
-          A.le2[0] = lm1 * c2.x; A.le2[1] = lm1 * c2.y; A.le2[2] = lm1 * c2.z;
-          A.lt[0] = lm1 * (c1.y * c2.z - c1.z * c2.y);
-          A.lt[1] = lm1 * (c1.z * c2.x - c1.x * c2.z);
-          A.lt[2] = lm1 * (c1.x * c2.y - c1.y * c2.x);
-          A.leps = -(dot3(c1, lc1) + dot3(c2, lc2)) / rc.eps;
+          S.le1[0] = lm1 * c1.x; S.le1[1] = lm1 * c1.y; S.le1[2] = lm1 * c1.z;
+          S.le2[0] = lm1 * c2.x; S.le2[1] = lm1 * c2.y; S.le2[2] = lm1 * c2.z;
+          S.lt[0] = lm1 * (c1.y * c2.z - c1.z * c2.y);
+          S.lt[1] = lm1 * (c1.z * c2.x - c1.x * c2.z);
+          S.lt[2] = lm1 * (c1.x * c2.y - c1.y * c2.x);
+          S.leps = -(dot3(c1, lc1) + dot3(c2, lc2)) / rc.eps;
           const float sc = P.h2_12 / rc.eps;
           lD1x = sc * lc1.x; lD1y = sc * lc1.y; lD1z = sc * lc1.z;
           lD2x = sc * lc2.x; lD2y = sc * lc2.y; lD2z = sc * lc2.z;
         }
+      } else if (central) {
+        A.lpos[0] = A.lpos[1] = A.lpos[2] = 0.f;
       }
-      // B: the neighbours reverse their retrace of step m (G enters d only)
-      Vec lp_n{0.f, 0.f, 0.f}, lk_n{0.f, 0.f, 0.f};
+      // B and C in one rk4_reverse pass: the neighbours reverse their
+      // retrace of step t (G enters the separations only), the central lane
+      // its own step t + 1
+      Vec rp{0.f, 0.f, 0.f}, rk{0.f, 0.f, 0.f}, lr_in{0.f, 0.f, 0.f}, lk_in{0.f, 0.f, 0.f}, lg{0.f, 0.f, 0.f};
+      Vec lp_o{0.f, 0.f, 0.f}, lk_o{0.f, 0.f, 0.f};
       if (NB > 0) {
-        const bool e = __shfl_sync(kFull, cw ? 1 : 0, base) != 0;
         const float g1x = __shfl_sync(kFull, lD1x, base), g1y = __shfl_sync(kFull, lD1y, base),
                     g1z = __shfl_sync(kFull, lD1z, base);
         const float g2x = __shfl_sync(kFull, lD2x, base), g2y = __shfl_sync(kFull, lD2y, base),
                     g2z = __shfl_sync(kFull, lD2z, base);
-        if (used && q > 0 && e) {
-          const StepRec& rc = R[j];
+        if (b_ok) {
+          const StepRec& rc = R[t];
           const float sgn = (q & 1) ? 1.f : -1.f;
           const bool first = q <= 2;
           const float* ev = first ? rc.e1 : rc.e2;
-          const Vec seed{rc.r[0] + sgn * rc.eps * ev[0], rc.r[1] + sgn * rc.eps * ev[1], rc.r[2] + sgn * rc.eps * ev[2]};
-          const Vec kk{rc.k[0], rc.k[1], rc.k[2]};
-          const Vec lg = first ? Vec{sgn * g1x, sgn * g1y, sgn * g1z} : Vec{sgn * g2x, sgn * g2y, sgn * g2z};
-          rk4_reverse(P.G, kf_lane, h, seed, kk, Vec{0.f, 0.f, 0.f}, Vec{0.f, 0.f, 0.f}, lg, lp_n, lk_n, P.dne);
+          rp = {rc.r[0] + sgn * rc.eps * ev[0], rc.r[1] + sgn * rc.eps * ev[1], rc.r[2] + sgn * rc.eps * ev[2]};
+          rk = {rc.k[0], rc.k[1], rc.k[2]};
+          lg = first ? Vec{sgn * g1x, sgn * g1y, sgn * g1z} : Vec{sgn * g2x, sgn * g2y, sgn * g2z};
         }
       }
-      // gather the seed adjoints to the central lane
-      Vec lps[4], lks[4];
-#pragma unroll
-      for (int n = 0; n < 4; ++n) {
-        lps[n] = {0.f, 0.f, 0.f};
-        lks[n] = {0.f, 0.f, 0.f};
+      if (c_ok) {
+        // C's inputs: the output adjoints of central step t + 1 and its seed/chord terms
+        const auto& S = A.st[(t + 1) & 1];
+        const bool last_step = last_seg && t + 1 == n_s - 1;
+        const StepRec& rc = R[t + 1];
+        Vec ldr{0.f, 0.f, 0.f};
         if (NB > 0) {
-          const int src = base + 1 + n;
-          lps[n] = {__shfl_sync(kFull, lp_n.x, src), __shfl_sync(kFull, lp_n.y, src), __shfl_sync(kFull, lp_n.z, src)};
-          lks[n] = {__shfl_sync(kFull, lk_n.x, src), __shfl_sync(kFull, lk_n.y, src), __shfl_sync(kFull, lk_n.z, src)};
-        }
-      }
-      if (cw) {
-        // C: seeds -> node m, chord, basis; then the central RK4 step reversed
-        const StepRec& rc = R[j];
-        Vec lrm{0.f, 0.f, 0.f}, lkm{0.f, 0.f, 0.f}, ldr{0.f, 0.f, 0.f};
-        if (NB > 0) {
-          const Vec e1{rc.e1[0], rc.e1[1], rc.e1[2]}, e2{rc.e2[0], rc.e2[1], rc.e2[2]}, t{rc.t[0], rc.t[1], rc.t[2]};
-          float leps = A.leps;
-          Vec le1{A.le1[0], A.le1[1], A.le1[2]}, le2{A.le2[0], A.le2[1], A.le2[2]}, lt{A.lt[0], A.lt[1], A.lt[2]};
-#pragma unroll
-          for (int n = 0; n < 4; ++n) {
-            lrm = {lrm.x + lps[n].x, lrm.y + lps[n].y, lrm.z + lps[n].z};
-            lkm = {lkm.x + lks[n].x, lkm.y + lks[n].y, lkm.z + lks[n].z};
-          }
-          leps += dot3(e1, lps[0]) - dot3(e1, lps[1]) + dot3(e2, lps[2]) - dot3(e2, lps[3]);
-          le1 = {le1.x + rc.eps * (lps[0].x - lps[1].x), le1.y + rc.eps * (lps[0].y - lps[1].y),
-                 le1.z + rc.eps * (lps[0].z - lps[1].z)};
-          le2 = {le2.x + rc.eps * (lps[2].x - lps[3].x), le2.y + rc.eps * (lps[2].y - lps[3].y),
-                 le2.z + rc.eps * (lps[2].z - lps[3].z)};
+          const Vec e1{rc.e1[0], rc.e1[1], rc.e1[2]}, t3{rc.t[0], rc.t[1], rc.t[2]};
+          lp_o = {S.slp[0], S.slp[1], S.slp[2]};
+          lk_o = {S.slk[0], S.slk[1], S.slk[2]};
+          Vec le1{S.le1[0], S.le1[1], S.le1[2]}, lt{S.lt[0], S.lt[1], S.lt[2]};
+          const Vec le2{S.le2[0], S.le2[1], S.le2[2]};
           // e2 = t x e1
           lt = {lt.x + (e1.y * le2.z - e1.z * le2.y), lt.y + (e1.z * le2.x - e1.x * le2.z),
                 lt.z + (e1.x * le2.y - e1.y * le2.x)};
-          le1 = {le1.x + (le2.y * t.z - le2.z * t.y), le1.y + (le2.z * t.x - le2.x * t.z),
-                 le1.z + (le2.x * t.y - le2.y * t.x)};
+          le1 = {le1.x + (le2.y * t3.z - le2.z * t3.y), le1.y + (le2.z * t3.x - le2.x * t3.z),
+                 le1.z + (le2.x * t3.y - le2.y * t3.x)};
           // e1 = c / |c|, c = a x t
           const Vec av = (rc.axis == 0) ? Vec{0.f, 0.f, 1.f} : Vec{0.f, 1.f, 0.f};
-          const Vec cv{av.y * t.z - av.z * t.y, av.z * t.x - av.x * t.z, av.x * t.y - av.y * t.x};
+          const Vec cv{av.y * t3.z - av.z * t3.y, av.z * t3.x - av.x * t3.z, av.x * t3.y - av.y * t3.x};
           const float ic = rsqrtf(dot3(cv, cv));
           const float pe = dot3(e1, le1);
           const Vec lc{(le1.x - pe * e1.x) * ic, (le1.y - pe * e1.y) * ic, (le1.z - pe * e1.z) * ic};
-          lt = {lt.x + (lc.y * av.z - lc.z * av.y), lt.y + (lc.z * av.x - lc.x * av.z), lt.z + (lc.x * av.y - lc.y * av.x)};
+          lt = {lt.x + (lc.y * av.z - lc.z * av.y), lt.y + (lc.z * av.x - lc.x * av.z),
+                lt.z + (lc.x * av.y - lc.y * av.x)};
           // eps = eta |dr| (Eq. 8); t = dr / |dr| (Eq. 5)
           const Vec dr{rc.dr[0], rc.dr[1], rc.dr[2]};
           const float ids = rsqrtf(dot3(dr, dr));
-          const float lds = (P.eps_fixed > 0.f) ? 0.f : P.eta * leps;
-          const float pt = dot3(t, lt);
-          ldr = {(lt.x - pt * t.x) * ids + t.x * lds, (lt.y - pt * t.y) * ids + t.y * lds,
-                 (lt.z - pt * t.z) * ids + t.z * lds};
+          const float lds = (P.eps_fixed > 0.f) ? 0.f : P.eta * S.leps;
+          const float pt = dot3(t3, lt);
+          ldr = {(lt.x - pt * t3.x) * ids + t3.x * lds, (lt.y - pt * t3.y) * ids + t3.y * lds,
+                 (lt.z - pt * t3.z) * ids + t3.z * lds};
         }
         Vec lr_next{A.lr[0], A.lr[1], A.lr[2]};
         if (last_step && A.clipped) {
           // clip point pc = r_m + alpha dr with |pc| = R: d alpha = -(pc . (d r_m + alpha d dr)) / (pc . dr)
-          const StepRec& rn = R[j + 1];
+          const StepRec& rn = R[t + 2];
           const Vec pc{rn.r[0], rn.r[1], rn.r[2]}, dr{rc.dr[0], rc.dr[1], rc.dr[2]};
-          const Vec lpc{A.lpc[0], A.lpc[1], A.lpc[2]};
+          const Vec lpc{S.lpc[0], S.lpc[1], S.lpc[2]};
           const float den = dot3(pc, dr);
-          const float la = A.lalpha + dot3(lpc, dr);
+          const float la = S.lalpha + dot3(lpc, dr);
           const float g = (den != 0.f) ? la / den : 0.f;
-          lrm = {lrm.x + lpc.x - g * pc.x, lrm.y + lpc.y - g * pc.y, lrm.z + lpc.z - g * pc.z};
+          lp_o = {lp_o.x + lpc.x - g * pc.x, lp_o.y + lpc.y - g * pc.y, lp_o.z + lpc.z - g * pc.z};
           ldr = {ldr.x + A.alpha * (lpc.x - g * pc.x), ldr.y + A.alpha * (lpc.y - g * pc.y),
                  ldr.z + A.alpha * (lpc.z - g * pc.z)};
           lr_next = {0.f, 0.f, 0.f};  // the unclipped node is used only through the chord
         }
         // dr = r' - r_m
-        const Vec lrp{lr_next.x + ldr.x, lr_next.y + ldr.y, lr_next.z + ldr.z};
-        lrm = {lrm.x - ldr.x, lrm.y - ldr.y, lrm.z - ldr.z};
-        const Vec lkp{A.lk[0], A.lk[1], A.lk[2]};
-        rk4_reverse(P.G, A.kf, h, Vec{rc.r[0], rc.r[1], rc.r[2]}, Vec{rc.k[0], rc.k[1], rc.k[2]}, lrp, lkp,
-                    Vec{0.f, 0.f, 0.f}, lrm, lkm, P.dne);
-        A.lr[0] = lrm.x; A.lr[1] = lrm.y; A.lr[2] = lrm.z;
-        A.lk[0] = lkm.x; A.lk[1] = lkm.y; A.lk[2] = lkm.z;
+        lr_in = {lr_next.x + ldr.x, lr_next.y + ldr.y, lr_next.z + ldr.z};
+        lp_o = {lp_o.x - ldr.x, lp_o.y - ldr.y, lp_o.z - ldr.z};
+        lk_in = {A.lk[0], A.lk[1], A.lk[2]};
+        rp = {rc.r[0], rc.r[1], rc.r[2]};
+        rk = {rc.k[0], rc.k[1], rc.k[2]};
+      }
+      if (c_ok || b_ok) rk4_reverse(P.G, kf_lane, h, rp, rk, lr_in, lk_in, lg, lp_o, lk_o, P.dne);
+      // gather the neighbours' seed adjoints of step t to the central lane
+      if (NB > 0) {
+        Vec lps[4], lks[4];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          const int src = base + 1 + n;
+          lps[n] = {__shfl_sync(kFull, lp_o.x, src), __shfl_sync(kFull, lp_o.y, src), __shfl_sync(kFull, lp_o.z, src)};
+          lks[n] = {__shfl_sync(kFull, lk_o.x, src), __shfl_sync(kFull, lk_o.y, src), __shfl_sync(kFull, lk_o.z, src)};
+        }
+        if (a_ok) {
+          // seeds r_m +- eps e_j with k = k_m: node, eps and basis adjoints of step t
+          auto& S = A.st[t & 1];
+          const StepRec& rc = R[t];
+          const Vec e1{rc.e1[0], rc.e1[1], rc.e1[2]}, e2{rc.e2[0], rc.e2[1], rc.e2[2]};
+#pragma unroll
+          for (int n = 0; n < 4; ++n) {
+            S.slp[0] += lps[n].x; S.slp[1] += lps[n].y; S.slp[2] += lps[n].z;
+            S.slk[0] += lks[n].x; S.slk[1] += lks[n].y; S.slk[2] += lks[n].z;
+          }
+          S.leps += dot3(e1, lps[0]) - dot3(e1, lps[1]) + dot3(e2, lps[2]) - dot3(e2, lps[3]);
+          S.le1[0] += rc.eps * (lps[0].x - lps[1].x);
+          S.le1[1] += rc.eps * (lps[0].y - lps[1].y);
+          S.le1[2] += rc.eps * (lps[0].z - lps[1].z);
+          S.le2[0] += rc.eps * (lps[2].x - lps[3].x);
+          S.le2[1] += rc.eps * (lps[2].y - lps[3].y);
+          S.le2[2] += rc.eps * (lps[2].z - lps[3].z);
+        }
+      }
+      // the adjoints at node m0 + t + 1: C's output plus A's value term
+      if (c_ok) {
+        A.lr[0] = lp_o.x + A.lpos[0]; A.lr[1] = lp_o.y + A.lpos[1]; A.lr[2] = lp_o.z + A.lpos[2];
+        A.lk[0] = lk_o.x; A.lk[1] = lk_o.y; A.lk[2] = lk_o.z;
+      } else if (a_ok) {
+        A.lr[0] += A.lpos[0]; A.lr[1] += A.lpos[1]; A.lr[2] += A.lpos[2];
       }
     }
 
