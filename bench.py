@@ -342,6 +342,8 @@ def main():
         ga, va, fa = cs.adjoint_workload()
         grid_a = ctx.load(ga)
         adjoint = {"workload": "Newkirk 128x90x180 grid, 256x256 x 8 freq 40-400 MHz, 4 neighbours"}
+        adjoint["ratio_definition"] = ("backward given the forward's per-ray diagnostics (the autograd path) / "
+                                       "forward; ratio_standalone: rt_backward with its own counting pass")
         for nm, pr in (("mixed", rt.RT_MIXED), ("plain", rt.RT_PLAIN_F32)):
             oa = rt.options(precision=pr)
             ctx.trace_image(grid_a, va, fa, oa)
@@ -350,14 +352,23 @@ def main():
             tbf = ctx.trace_image(grid_a, va, fa, oa)
             torch.cuda.synchronize()
             tf = time.perf_counter() - t0
-            wgt = torch.ones_like(tbf)
-            ctx.backward(grid_a, va, fa, wgt, oa)
+            t0 = time.perf_counter()
+            tbf, dg = ctx.trace_image(grid_a, va, fa, oa, diag=True)
             torch.cuda.synchronize()
+            tfd = time.perf_counter() - t0
+            wgt = torch.ones_like(tbf)
+            ctx.backward(grid_a, va, fa, wgt, oa, fwd_diag=dg)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.backward(grid_a, va, fa, wgt, oa, fwd_diag=dg)
+            torch.cuda.synchronize()
+            tbk = time.perf_counter() - t0
             t0 = time.perf_counter()
             ctx.backward(grid_a, va, fa, wgt, oa)
             torch.cuda.synchronize()
-            tbk = time.perf_counter() - t0
-            adjoint[nm] = {"forward_s": tf, "backward_s": tbk, "ratio": tbk / tf}
+            tbs = time.perf_counter() - t0
+            adjoint[nm] = {"forward_s": tf, "forward_diag_s": tfd, "backward_s": tbk, "ratio": tbk / tf,
+                           "backward_standalone_s": tbs, "ratio_standalone": tbs / tf}
         grid_a.free()
 
     peaks, peak_src = load_peaks()

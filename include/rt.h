@@ -209,22 +209,30 @@ rt_status rt_trace_batch(rt_ctx* ctx, const rt_grid* grid, const rt_request* req
  * dL_dTb * T_b, returns dL/dn_e and dL/dT_e at every grid node, exact for
  * the discrete forward computation with its discrete events held fixed
  * (cell indices, the basis axis branch, the step count, the termination
- * step).  Internally: the forward pass, a second forward pass that stores
- * the ray state every 32 central steps, then a reverse sweep that recomputes
- * each 32-step segment and runs the transfer, tube-area, neighbour-retrace
- * and RK4 adjoints back through it, scattering node gradients with atomics.
+ * step).  Internally: the forward pass (skipped when fwd_diag is given), a
+ * second forward pass that stores the ray state every 32 central steps, then
+ * a reverse sweep that recomputes each 32-step segment and runs the
+ * transfer, tube-area, neighbour-retrace and RK4 adjoints back through it,
+ * scattering node gradients with atomics.
  * view, freqs_hz, nf, opt: as for rt_trace_image; supported forms: s_mode
  * RT_STEPWISE with n_nb = 4, or RT_MAG_OFF; not straight lines of sight.
  * dL_dTb:  device [nf][ny][nx] float.
  * dL_dne, dL_dte: device [n_r][n_theta][n_phi] float, caller-owned,
  *          overwritten (zeroed by the call first).
  * tb_out:  device [nf][ny][nx] float for the forward T_b, or NULL.
+ * fwd_diag: optional device [nf][ny][nx] rt_ray_diag that rt_trace_image
+ *          returned for the same grid, view, frequencies and options (an
+ *          autograd forward keeps it).  The checkpoints are sized from its
+ *          step counts and the first forward pass is skipped.  NULL: the
+ *          call traces the rays once more to count their steps.  A diag
+ *          whose step counts differ from this forward's gives RT_ERR_ARG
+ *          (no ray reads another ray's checkpoints).
  * Synchronous: returns when the gradients are complete.  Allocates and
  * frees its own device scratch (checkpoints ~ total ray steps / 32 x 64 B).
  * Errors: RT_ERR_ARG, RT_ERR_UNSUPPORTED, RT_ERR_OOM, RT_ERR_CUDA. */
 rt_status rt_backward(rt_ctx* ctx, const rt_grid* grid, const rt_view* view, const double* freqs_hz, int nf,
                       const rt_options* opt, const float* dL_dTb, float* dL_dne, float* dL_dte, float* tb_out,
-                      void* stream);
+                      const rt_ray_diag* fwd_diag, void* stream);
 
 /* Allocation-free batch.  The paper has no counterpart: this entry point
  * exists for callers that must not allocate device memory when they trace,

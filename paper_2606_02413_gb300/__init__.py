@@ -195,10 +195,12 @@ class Context:
         """rt_batch_plan_create over requests (objects with .view and .freqs_hz)."""
         return BatchPlan(self, grid, requests, opts, diag)
 
-    def backward(self, grid: Grid, v, freqs, dL_dTb, opts=None, want_tb=False, stream=None):
+    def backward(self, grid: Grid, v, freqs, dL_dTb, opts=None, want_tb=False, fwd_diag=None, stream=None):
         """rt_backward: gradients of sum(dL_dTb * T_b) w.r.t. the grid node
         values.  Returns (dL/dn_e, dL/dT_e) as float32 CUDA tensors shaped like
-        the grid (and the forward T_b with want_tb=True)."""
+        the grid (and the forward T_b with want_tb=True).  fwd_diag: the diag
+        tensor of trace_image(..., diag=True) for the same inputs, which spares
+        the call its step-counting forward pass."""
         import torch
         vs = view(v)
         f = np.ascontiguousarray(np.atleast_1d(freqs), dtype=np.float64)
@@ -209,9 +211,12 @@ class Context:
         dte = torch.empty(grid.shape, dtype=torch.float32, device=dev)
         tb = torch.empty((len(f), vs.ny, vs.nx), dtype=torch.float32, device=dev) if want_tb else None
         o = opts if opts is not None else options()
+        if fwd_diag is not None:
+            assert fwd_diag.is_cuda and fwd_diag.is_contiguous() and fwd_diag.numel() * 4 == 28 * g.numel()
         check(lib().rt_backward(self.handle, grid.handle, C.byref(vs), f.ctypes.data_as(C.POINTER(C.c_double)),
                                 len(f), C.byref(o), C.c_void_p(g.data_ptr()), C.c_void_p(dne.data_ptr()),
                                 C.c_void_p(dte.data_ptr()), C.c_void_p(tb.data_ptr() if tb is not None else 0),
+                                C.c_void_p(fwd_diag.data_ptr() if fwd_diag is not None else 0),
                                 _stream_ptr(stream)), "rt_backward")
         return (dne, dte, tb) if want_tb else (dne, dte)
 
@@ -258,14 +263,14 @@ class RayTraceFn:
             @staticmethod
             def forward(fctx, ne, te, ctx, r, theta, phi, v, freqs, opts):
                 grid = ctx.load_grid(r, theta, phi, ne.detach(), te.detach())
-                tb = ctx.trace_image(grid, v, freqs, opts)
-                fctx.state = (ctx, grid, v, freqs, opts, ne.dtype, te.dtype)
+                tb, d = ctx.trace_image(grid, v, freqs, opts, diag=True)
+                fctx.state = (ctx, grid, v, freqs, opts, ne.dtype, te.dtype, d)
                 return tb
 
             @staticmethod
             def backward(fctx, grad_tb):
-                ctx, grid, v, freqs, opts, dne_t, dte_t = fctx.state
-                dne, dte = ctx.backward(grid, v, freqs, grad_tb.contiguous(), opts)
+                ctx, grid, v, freqs, opts, dne_t, dte_t, d = fctx.state
+                dne, dte = ctx.backward(grid, v, freqs, grad_tb.contiguous(), opts, fwd_diag=d)
                 grid.free()
                 return dne.to(dne_t), dte.to(dte_t), None, None, None, None, None, None, None
 

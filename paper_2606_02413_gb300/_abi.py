@@ -94,7 +94,7 @@ def lib():
                                      C.POINTER(Options), vp, vp, vp]
         L.rt_probe_field.argtypes = [vp, vp, vp, ip, vp, vp]
         L.rt_backward.argtypes = [vp, vp, C.POINTER(View), C.POINTER(C.c_double), ip, C.POINTER(Options),
-                                  vp, vp, vp, vp, vp]
+                                  vp, vp, vp, vp, vp, vp]
         L.rt_batch_plan_create.argtypes = [vp, vp, C.POINTER(Request), ip, C.POINTER(Options), C.POINTER(vp)]
         L.rt_batch_plan_launch.argtypes = [vp, vp]
         L.rt_batch_plan_stats.argtypes = [vp, vp, C.POINTER(Stats)]

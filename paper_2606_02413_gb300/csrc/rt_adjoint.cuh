@@ -284,6 +284,7 @@ struct AdjParams {
   float* dte;
   unsigned int* counter;
   unsigned int total;
+  unsigned long long* mismatch;  // rays whose step count does not match their checkpoint allocation
 };
 
 struct AdjState {
@@ -348,8 +349,11 @@ __global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_bundles(const
           const size_t o = (size_t)F.out_slab * P.view.npix + pix;
           const RayDiag d = P.diag[o];
           const float lamT = P.dL_dTb[o];
-          const bool has = d.steps > 0 && d.status >= kExitOuter && d.status <= kStepLimit && lamT != 0.f &&
-                           P.ck_off[item + 1] > P.ck_off[item];
+          // the checkpoints were sized from a step count: it must be this ray's
+          const unsigned long long n_ck = (d.steps > 0) ? (unsigned long long)((d.steps - 1) / K + 1) : 0ull;
+          const bool fits = P.ck_off[item + 1] - P.ck_off[item] == n_ck;
+          if (!fits) atomicAdd(P.mismatch, 1ull);
+          const bool has = fits && d.steps > 0 && d.status >= kExitOuter && d.status <= kStepLimit && lamT != 0.f;
           if (has) {
             A.N = d.steps;
             A.status = d.status;

@@ -734,7 +734,8 @@ rt_status rt_trace_batch(rt_ctx* ctx, const rt_grid* g, const rt_request* reqs, 
 }
 
 rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const double* freqs, int nf, const rt_options* o,
-                      const float* dL_dTb, float* dL_dne, float* dL_dte, float* tb_out, void* stream) {
+                      const float* dL_dTb, float* dL_dne, float* dL_dte, float* tb_out, const rt_ray_diag* fwd_diag,
+                      void* stream) {
   if (!ctx || !g || !freqs || !dL_dTb || !dL_dne || !dL_dte) return fail(RT_ERR_ARG, "rt_backward: NULL argument");
   rt_status st = check_view(v);
   if (st != RT_OK) return st;
@@ -768,7 +769,8 @@ rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const dou
   };
   cudaError_t e = cudaMalloc(&diag, sizeof(RayDiag) * total);
   if (e == cudaSuccess && !tb_out) e = cudaMalloc(&tb, sizeof(float) * total);
-  if (e == cudaSuccess) e = cudaMalloc(&ck_off, sizeof(unsigned long long) * (total + 1));
+  // checkpoint offsets [total + 1] and, behind them, the adjoint's mismatch flag
+  if (e == cudaSuccess) e = cudaMalloc(&ck_off, sizeof(unsigned long long) * (total + 2));
   if (e != cudaSuccess) {
     release();
     return fail(e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "rt_backward: %s", cudaGetErrorString(e));
@@ -796,9 +798,14 @@ rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const dou
     if (r == cudaSuccess) r = dispatch_trace(nb, mixed, P, ctx->sm_count, s);
     return r;
   };
-  e = run_forward();
   std::vector<RayDiag> hd(total);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hd.data(), diag, sizeof(RayDiag) * total, cudaMemcpyDeviceToHost, s);
+  if (fwd_diag) {  // the caller's forward already counted the steps
+    static_assert(sizeof(RayDiag) == sizeof(rt_ray_diag), "rt_ray_diag layout");
+    e = cudaMemcpyAsync(hd.data(), fwd_diag, sizeof(RayDiag) * total, cudaMemcpyDeviceToHost, s);
+  } else {
+    e = run_forward();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hd.data(), diag, sizeof(RayDiag) * total, cudaMemcpyDeviceToHost, s);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     release();
@@ -818,6 +825,7 @@ rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const dou
   if (e == cudaSuccess) e = cudaMalloc(&rec, sizeof(StepRec) * slots * (kCkptEvery + 1));
   if (e == cudaSuccess) e = cudaMemcpyAsync(ck_off, off.data(), sizeof(unsigned long long) * (total + 1),
                                             cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ck_off + total + 1, 0, sizeof(unsigned long long), s);
   // phase 1: the same forward again, storing checkpoints
   P.ckpt = ckpt;
   P.ck_off = ck_off;
@@ -844,14 +852,21 @@ rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const dou
     A.dte = dL_dte;
     A.counter = ctx->d_counter;
     A.total = (unsigned int)total;
+    A.mismatch = ck_off + total + 1;
     if (nb == 0) adjoint_bundles<0><<<grid_blocks, kThreads, 0, s>>>(A);
     else adjoint_bundles<4><<<grid_blocks, kThreads, 0, s>>>(A);
     e = cudaGetLastError();
   }
+  unsigned long long mismatch = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&mismatch, ck_off + total + 1, sizeof mismatch, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   release();
   if (e != cudaSuccess)
     return fail(e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "rt_backward: %s", cudaGetErrorString(e));
+  if (mismatch)
+    return fail(RT_ERR_ARG, "rt_backward: fwd_diag does not match this forward (%llu rays with other step counts)",
+                mismatch);
   return RT_OK;
 }
 

@@ -101,3 +101,24 @@ def test_autograd_function(rt, ctx):
     torch.cuda.synchronize()
     assert torch.allclose(ne.grad, dne, rtol=1e-5, atol=1e-30 + 1e-6 * dne.abs().max().item())
     assert torch.allclose(te.grad, dte, rtol=1e-5, atol=1e-30 + 1e-6 * dte.abs().max().item())
+
+
+def test_backward_reuses_forward_diag(rt, ctx):
+    """fwd_diag (the forward's step counts) spares the counting pass and gives
+    the same gradients; a diag of another forward is refused."""
+    import torch
+    g = smooth_grid()
+    v = cs.View(0.3, 0.1, 6, 5, -1.8, 1.8, -1.6, 1.6)
+    grid = ctx.load(g)
+    opts = rt.options(precision=1, dtau=1e-2)
+    w = torch.as_tensor(np.random.default_rng(4).normal(size=(1, v.ny, v.nx)), dtype=torch.float32, device="cuda")
+    _, d = ctx.trace_image(grid, v, [60e6], opts, diag=True)
+    a = ctx.backward(grid, v, [60e6], w, opts, fwd_diag=d)
+    b = ctx.backward(grid, v, [60e6], w, opts)
+    torch.cuda.synchronize()
+    for x, y in zip(a, b):  # equal up to the order of the float atomics
+        assert torch.allclose(x, y, rtol=1e-4, atol=1e-30 + 1e-5 * y.abs().max().item())
+    _, d_other = ctx.trace_image(grid, v, [400e6], opts, diag=True)  # other frequency: other step counts
+    assert not torch.equal(d_other[..., 5], d[..., 5])
+    with pytest.raises(RuntimeError, match="fwd_diag"):
+        ctx.backward(grid, v, [60e6], w, opts, fwd_diag=d_other)
