@@ -126,6 +126,20 @@ def shard_views(base_view, world_size: int, rank: int):
                    v.x0, v.x1, v.y0, v.y1)
 
 
+def reduce_over_ranks(total_ms: float, ray_steps: float, world_size: int, device="cpu"):
+    """The job's time is the slowest rank's, its work the sum over ranks
+    (weak scaling: no data-path collective, only this reduction of two
+    numbers after the timed region)."""
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(ray_steps)], dtype=torch.float64, device=device)
+    if world_size > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
 def cpu_baseline(g, v, f, target_s=12.0, max_pixels=4096):
     """The FP64 oracle (as it stands) on a bounded pixel sample of the same
     workload, on this host's cores; ray-steps/s and the sample description."""
@@ -179,8 +193,9 @@ def run_profile_case(name):
     """One launch of a named case, small enough for an ncu capture.
     fwd-WxHxF: the headline corona, a WxH view over +-3 R_sun at 60 and 300
     MHz, compensated form.  adj-WxHxF: rt_backward on the 128x90x180
-    differentiation corona, a WxH view over +-2.5 R_sun at 60 and 200 MHz
-    (adj-256x256x8: the full differentiation workload), dL/dT_b = 1."""
+    differentiation corona, a WxH view over +-2.5 R_sun at F of its 8
+    frequencies (40-400 MHz, evenly picked; adj-256x256x8 is the full
+    differentiation workload), dL/dT_b = 1."""
     import torch
 
     import corona_synth as cs
@@ -198,9 +213,8 @@ def run_profile_case(name):
     else:
         g, v, f = cs.adjoint_workload()
         grid = ctx.load(g)
-        if nf != len(f):
-            v = cs.View(0.0, 0.0, nx, ny, -2.5, 2.5, -2.5, 2.5)
-            f = [60e6, 200e6][:nf]
+        v = cs.View(v.lon_rad, v.lat_rad, nx, ny, v.x0, v.x1, v.y0, v.y1)
+        f = [float(f[i]) for i in np.linspace(0, len(f) - 1, min(nf, len(f))).round().astype(int)]
         ctx.backward(grid, v, f, torch.ones((len(f), v.ny, v.nx), device="cuda"), rt.options(precision=rt.RT_MIXED))
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": name, "stats": ctx.stats()}))
@@ -217,7 +231,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--profile-case", default=None,
-                    choices=["fwd-128x128x2", "fwd-256x256x2", "adj-64x64x2", "adj-256x256x8"],
+                    choices=["fwd-128x128x2", "fwd-256x256x2", "adj-64x64x2", "adj-128x128x8", "adj-256x256x8"],
                     help="run one launch of a small named case (for ncu captures) and exit")
     ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
@@ -276,15 +290,7 @@ def main():
     ray_steps = stats["ray_steps"] * args.steps
     total_ms = t_start.elapsed_time(t_end)
     kern_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    t = torch.tensor([total_ms], dtype=torch.float64)
-    steps_t = torch.tensor([float(ray_steps)], dtype=torch.float64)
-    if ws > 1:
-        t = t.cuda()
-        steps_t = steps_t.cuda()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(steps_t, op=dist.ReduceOp.SUM)
-    total_ms = float(t.item())
-    all_steps = float(steps_t.item())
+    total_ms, all_steps = reduce_over_ranks(total_ms, ray_steps, ws, device=f"cuda:{local}")
     value = all_steps / (total_ms / 1e3)
     maps_per_s = len(f) * ws * args.steps / (total_ms / 1e3)
 
