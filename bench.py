@@ -126,6 +126,38 @@ def shard_views(base_view, world_size: int, rank: int):
                    v.x0, v.x1, v.y0, v.y1)
 
 
+def kernel_source_hash() -> str:
+    """Hash of the CUDA sources (file names and contents) the library is
+    built from: a committed counter capture is valid only for this hash."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2606_02413_gb300", "csrc", "*.cu*"))):
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "trace_bundles_global_512x512x16_launches.md")
+
+
+def committed_traffic():
+    """DRAM bytes per launch of the headline kernel from the committed ncu
+    launch list (line 'traffic: source=<hash> bytes_per_launch=<n>'), or
+    None when the kernel sources changed since that capture."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            for line in fh:
+                if line.startswith("traffic:"):
+                    kv = dict(item.split("=", 1) for item in line.split()[1:])
+                    if kv.get("source") == kernel_source_hash():
+                        return float(kv["bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
 def reduce_over_ranks(total_ms: float, ray_steps: float, world_size: int, device="cpu"):
     """The job's time is the slowest rank's, its work the sum over ranks
     (weak scaling: no data-path collective, only this reduction of two
@@ -220,6 +252,28 @@ def run_profile_case(name):
     print(json.dumps({"profile_case": name, "stats": ctx.stats()}))
 
 
+def run_autotune():
+    """The autotuner on the headline workload (compensated form, 4
+    step-wise neighbours): step-size gate against the dtau = 1e-3 maps on a
+    32x32 image, launch shape timed on 128x128 x 16 maps."""
+    import torch
+
+    import corona_synth as cs
+    from paper_2606_02413_gb300 import build as rt_build
+    rt_build.build()
+    import paper_2606_02413_gb300 as rt
+    from paper_2606_02413_gb300 import autotune
+    ctx = rt.Context(0)
+    g, v, f = cs.global_workload()
+    grid = ctx.load(g)
+    t0 = time.perf_counter()
+    opts, report = autotune.tune(ctx, grid, v, f, rt.options(precision=rt.RT_MIXED), gate=1e-3)
+    torch.cuda.synchronize()
+    report["tuning_s"] = time.perf_counter() - t0
+    report["workload"] = "MAS-like 256x180x360, 512x512 x 16 freq 40-800 MHz, 4 step-wise neighbours, compensated"
+    print(json.dumps({"autotune": report}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -234,12 +288,17 @@ def main():
                     choices=["fwd-128x128x2", "fwd-256x256x2", "adj-64x64x2", "adj-128x128x8", "adj-256x256x8"],
                     help="run one launch of a small named case (for ncu captures) and exit")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="run the autotuner on the headline workload, print its report and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     if args.profile_case:
         run_profile_case(args.profile_case)
+        return
+    if args.autotune:
+        run_autotune()
         return
 
     import torch
@@ -385,7 +444,9 @@ def main():
     kmean = float(np.mean(kern_ms))
     achieved = flop_step * stats["ray_steps"] / (kmean / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": None,
+            "frac": achieved / fp32_peak, "traffic": committed_traffic(),
+            "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum per launch, "
+                              + os.path.relpath(TRAFFIC_FILE, ROOT) + " (null if the kernel changed)",
             "peak_source": f"FP32 FMA: 128 lanes x {n_sm} SMs x 2 x {clk:.0f} MHz median SM clock under load",
             "flop_per_ray_step": flop_step, "kernel": "trace_bundles<4, mixed>", "kernel_ms": kmean}
 
