@@ -50,7 +50,7 @@ enum {
   RT_ERR_OOM = -4,      /* device allocation failed                              */
   RT_ERR_TIMEOUT = -5,  /* a bounded device wait expired                         */
   RT_ERR_CHECKED = -6,  /* a device-side bounds check recorded a violation       */
-  RT_ERR_UNSUPPORTED = -7 /* valid request this build does not implement        */
+  RT_ERR_UNSUPPORTED = -7 /* a valid request the library does not implement    */
 };
 
 enum { RT_F32 = 0, RT_F64 = 1 };                       /* grid value types        */
