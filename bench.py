@@ -274,6 +274,73 @@ def run_autotune():
     print(json.dumps({"autotune": report}))
 
 
+def run_batch_workload():
+    """The batching workload: 64 independent requests on the symmetric
+    64x32x64 corona (image side in {128, 256, 512, 1024}, 1-8 frequencies in
+    40-800 MHz, random longitude; ~1e8 rays of very uneven length), plain
+    FP32 stepping, 4 step-wise neighbours; and, for contrast, 512 small
+    requests (sides 16-64) that one launch each would leave the GPU mostly
+    idle for.  Times one graph-captured persistent launch over each batch
+    against one rt_trace_image per request on the same stream, and checks
+    that the two give the same maps."""
+    import torch
+
+    import corona_synth as cs
+    from paper_2606_02413_gb300 import build as rt_build
+    rt_build.build()
+    import paper_2606_02413_gb300 as rt
+    ctx = rt.Context(0)
+    g, _, _ = cs.tiny_workload()
+    grid = ctx.load(g)
+    opts = rt.options(precision=rt.RT_PLAIN_F32)
+    stream = torch.cuda.current_stream()
+    # warm both paths on a small batch (kernel load, graph machinery)
+    small = cs.batch_requests(4, sides=(32,))
+    wp = ctx.batch_plan(grid, small, opts)
+    wp.launch()
+    for r in small:
+        ctx.trace_image(grid, r.view, r.freqs_hz, opts)
+    torch.cuda.synchronize()
+    wp.destroy()
+
+    def timed(fn):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    def measure(reqs, label):
+        n_maps = sum(len(r.freqs_hz) for r in reqs)
+        n_rays = sum(len(r.freqs_hz) * r.view.nx * r.view.ny for r in reqs)
+        plan = ctx.batch_plan(grid, reqs, opts)
+        ms_b = timed(plan.launch)
+        steps = plan.stats()["ray_steps"]
+        outs = [torch.empty((len(r.freqs_hz), r.view.ny, r.view.nx), dtype=torch.float32, device="cuda")
+                for r in reqs]
+
+        def sequential():
+            for r, o in zip(reqs, outs):
+                ctx.trace_image(grid, r.view, r.freqs_hz, opts, out=o)
+        ms_s = timed(sequential)
+        same = all(torch.equal(x, y) for x, y in zip(plan.outputs, outs))
+        plan.destroy()
+        return {"requests": len(reqs), "what": label, "maps": n_maps, "rays": n_rays, "ray_steps": steps,
+                "batched_ms": ms_b, "batched_maps_per_s": n_maps / (ms_b / 1e3),
+                "batched_ray_steps_per_s": steps / (ms_b / 1e3),
+                "per_request_ms": ms_s, "per_request_maps_per_s": n_maps / (ms_s / 1e3),
+                "per_request_ray_steps_per_s": steps / (ms_s / 1e3),  # the same rays, ray for ray
+                "speedup": ms_s / ms_b, "identical_maps": bool(same)}
+
+    out = {"form": "plain FP32, 4 step-wise neighbours, h = 2e-3 R_sun, 64x32x64 corona",
+           "batch_64": measure(cs.batch_requests(64), "sides 128-1024, 1-8 frequencies"),
+           "batch_512_small": measure(cs.batch_requests(512, sides=(16, 32, 64)), "sides 16-64, 1-8 frequencies")}
+    print(json.dumps({"batch_workload": out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -288,6 +355,8 @@ def main():
                     choices=["fwd-128x128x2", "fwd-256x256x2", "adj-64x64x2", "adj-128x128x8", "adj-256x256x8"],
                     help="run one launch of a small named case (for ncu captures) and exit")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--batch-workload", action="store_true",
+                    help="time the 64-request batching workload batched and per request, print and exit")
     ap.add_argument("--autotune", action="store_true",
                     help="run the autotuner on the headline workload, print its report and exit")
     args = ap.parse_args()
@@ -299,6 +368,9 @@ def main():
         return
     if args.autotune:
         run_autotune()
+        return
+    if args.batch_workload:
+        run_batch_workload()
         return
 
     import torch
