@@ -457,14 +457,14 @@ __global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_bundles(const
         }
         float e;
         float nx, ny, nz;
-        two_sum(px, dr.x + rlx, nx, e); rlx = e;
-        two_sum(py, dr.y + rly, ny, e); rly = e;
-        two_sum(pz, dr.z + rlz, nz, e); rlz = e;
+        fast_two_sum(px, dr.x + rlx, nx, e); rlx = e;
+        fast_two_sum(py, dr.y + rly, ny, e); rly = e;
+        fast_two_sum(pz, dr.z + rlz, nz, e); rlz = e;
         px = nx; py = ny; pz = nz;
         float mx, my, mz;
-        two_sum(kx, dk.x + klx, mx, e); klx = e;
-        two_sum(ky, dk.y + kly, my, e); kly = e;
-        two_sum(kz, dk.z + klz, mz, e); klz = e;
+        fast_two_sum(kx, dk.x + klx, mx, e); klx = e;
+        fast_two_sum(ky, dk.y + kly, my, e); kly = e;
+        fast_two_sum(kz, dk.z + klz, mz, e); klz = e;
         kx = mx; ky = my; kz = mz;
       }
       if (NB > 0) {

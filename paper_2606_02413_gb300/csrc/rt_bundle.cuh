@@ -529,12 +529,12 @@ __global__ void __launch_bounds__(kThreads, kTube ? kMinBlocksTube : kMinBlocks)
           Vec rn, kn;
           if (kMixed) {
             float e;
-            two_sum(px, dr.x + rlx, rn.x, e); rlx = e;
-            two_sum(py, dr.y + rly, rn.y, e); rly = e;
-            two_sum(pz, dr.z + rlz, rn.z, e); rlz = e;
-            two_sum(kx, dk.x + klx, kn.x, e); klx = e;
-            two_sum(ky, dk.y + kly, kn.y, e); kly = e;
-            two_sum(kz, dk.z + klz, kn.z, e); klz = e;
+            fast_two_sum(px, dr.x + rlx, rn.x, e); rlx = e;
+            fast_two_sum(py, dr.y + rly, rn.y, e); rly = e;
+            fast_two_sum(pz, dr.z + rlz, rn.z, e); rlz = e;
+            fast_two_sum(kx, dk.x + klx, kn.x, e); klx = e;
+            fast_two_sum(ky, dk.y + kly, kn.y, e); kly = e;
+            fast_two_sum(kz, dk.z + klz, kn.z, e); klz = e;
             B.rl[0] = rlx; B.rl[1] = rly; B.rl[2] = rlz;
             B.kl[0] = klx; B.kl[1] = kly; B.kl[2] = klz;
           } else {

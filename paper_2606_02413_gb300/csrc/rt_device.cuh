@@ -405,6 +405,16 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+// a + b = s + e with three operations (Fast2Sum, Dekker 1971): exact when
+// the exponent of a is at least that of b.  Used for a ray's position and
+// wave vector, whose components outweigh their per-step increments except
+// where a component passes within about one increment of zero; there e is
+// off by at most an ulp of the increment (~1e-10), once, not accumulating.
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+
 // Running sum.  kComp = true keeps the rounding error of every addition
 // (TwoSum) and carries it, so 10^4-term sums stay near double precision;
 // kComp = false is the plain FP32 sum.
