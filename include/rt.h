@@ -235,26 +235,31 @@ rt_status rt_backward(rt_ctx* ctx, const rt_grid* grid, const rt_view* view, con
                       const rt_ray_diag* fwd_diag, void* stream);
 
 /* Allocation-free batch.  The paper has no counterpart: this entry point
- * exists for callers that must not allocate device memory when they trace,
- * such as code running while a CUDA stream is being captured into a graph
- * (where cudaMalloc is not allowed), real-time loops that run on a fixed
- * memory budget, or hosts whose device memory belongs to another allocator.
- * It computes exactly what rt_trace_batch computes, but its scratch (the
- * work-queue ticket, the ray counters and the request/map/chunk tables) lives
- * in one file-scope device array of RT_NOALLOC_SCRATCH_BYTES (2 MiB) that
- * every GPU loading the library holds until the process exits; it calls no
- * cudaMalloc, cudaFree or allocating library routine.
- *   - Runs on the calling thread's current device, which must hold `grid`
- *     (loaded earlier with rt_load_grid; the caller passes inputs and
- *     outputs as for rt_trace_batch, no context is needed).
+ * exists for callers that cannot allocate device memory when they trace:
+ * real-time loops that must not stall (cudaMalloc and cudaFree synchronise
+ * the device and can take milliseconds) or that run on a memory budget fixed
+ * at start-up, and hosts whose device memory is all owned by another
+ * allocator (a framework's caching pool), where a cudaMalloc of the library
+ * can fail or fragment that pool.  It computes what rt_trace_batch computes,
+ * but its scratch (the work-queue ticket, the ray counters and the
+ * request/map/chunk tables) lives in one file-scope device array of
+ * RT_NOALLOC_SCRATCH_BYTES (2 MiB) that every GPU loading the library holds
+ * until the process exits; it calls no cudaMalloc, cudaFree or allocating
+ * library routine, and stages its tables in static host memory.
+ *   - Runs on the calling thread's current device, which must be the device
+ *     that holds `grid` (loaded earlier with rt_load_grid; otherwise
+ *     RT_ERR_ARG).  The caller passes inputs and outputs as for
+ *     rt_trace_batch; no context is needed.
  *   - The first call on a device looks up the array's device address (and
- *     loads the library's kernels there); make that first call before any
- *     stream capture.
- *   - All calls share the array: calls whose work overlaps on the GPU race
- *     and give wrong results.  Serialise them (one stream, or events).
- *   - Asynchronous on `stream`; the host tables are copied before return.
- * Errors: RT_ERR_ARG (bad request, or the tables of this batch need more
- * than RT_NOALLOC_SCRATCH_BYTES: about 100k chunks of 64 pixels),
+ *     loads the library's kernels there).
+ *   - All calls share the array, which keeps the last call's contents (the
+ *     call clears the ticket and counters itself).  Calls whose work
+ *     overlaps on the GPU race and give wrong results: issue them on one
+ *     stream, or order them with events.
+ *   - Asynchronous on `stream`; the host tables have been copied when the
+ *     call returns.
+ * Errors: RT_ERR_ARG (bad request, wrong device, or the tables of this batch
+ * need more than RT_NOALLOC_SCRATCH_BYTES: about 100k chunks of 64 pixels),
  * RT_ERR_CUDA. */
 #define RT_NOALLOC_SCRATCH_BYTES (2u << 20)
 rt_status rt_trace_batch_noalloc(const rt_grid* grid, const rt_request* reqs, int nreq,

@@ -65,6 +65,7 @@ struct rt_ctx {
 
 struct rt_grid {
   GridDev dev{};
+  int device = 0;                // CUDA device that holds the grid
   float4* ne = nullptr;
   float4* te = nullptr;
   int2* lut = nullptr;
@@ -336,6 +337,7 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
   RT_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   rt_grid* g = new rt_grid;
+  g->device = ctx->device;
   g->n_r = nr; g->n_t = nt; g->n_p = np;
   const long ncell = (long)(nr - 1) * (nt - 1) * np;
   const size_t esz = d->dtype == RT_F64 ? 8 : 4;
@@ -921,6 +923,21 @@ NoAllocDevice g_noalloc_devices[kMaxDevices];
 
 size_t align16(size_t n) { return (n + 15) & ~size_t(15); }
 
+// Host staging of the tables, also static: the call allocates no host memory
+// either.  One image of the device scratch, and the chunk candidates with
+// their length estimates for the longest-first order.  The mutex serialises
+// callers on different threads while they fill and copy it (a pageable
+// cudaMemcpyAsync has read its source when it returns).
+constexpr size_t kNoAllocMaxChunks = RT_NOALLOC_SCRATCH_BYTES / sizeof(ChunkDev);
+struct NoAllocCand {
+  double cost;
+  unsigned int order;  // position in the request order: ties keep it
+  ChunkDev c;
+};
+alignas(256) unsigned char g_noalloc_image[RT_NOALLOC_SCRATCH_BYTES];
+NoAllocCand g_noalloc_cands[kNoAllocMaxChunks];
+std::mutex g_noalloc_host_mutex;
+
 }  // namespace
 
 extern "C" rt_status rt_trace_batch_noalloc(const rt_grid* g, const rt_request* reqs, int nreq, const rt_options* o,
@@ -932,6 +949,9 @@ extern "C" rt_status rt_trace_batch_noalloc(const rt_grid* g, const rt_request* 
   if (st != RT_OK) return st;
   int dev = 0;
   RT_CUDA(cudaGetDevice(&dev));
+  if (dev != g->device)
+    return fail(RT_ERR_ARG, "rt_trace_batch_noalloc: the current device is %d, the grid lives on device %d", dev,
+                g->device);
   if (dev < 0 || dev >= kMaxDevices) return fail(RT_ERR_ARG, "rt_trace_batch_noalloc: device %d", dev);
   NoAllocDevice& D = g_noalloc_devices[dev];
   std::call_once(D.once, [&D, dev]() {
@@ -943,56 +963,65 @@ extern "C" rt_status rt_trace_batch_noalloc(const rt_grid* g, const rt_request* 
   if (D.err != cudaSuccess || !D.scratch)
     return fail(RT_ERR_CUDA, "rt_trace_batch_noalloc: scratch set-up failed: %s", cudaGetErrorString(D.err));
 
-  // tables: one view per request, one map per (request, frequency), chunks
-  // of up to kChunk pixels ordered longest-first
-  std::vector<ViewDev> views;
-  std::vector<MapDev> maps;
-  std::vector<std::pair<double, ChunkDev>> cands;
-  const double rmin = g->r.front(), rmax = g->r.back();
+  // sizes first: one view per request, one map per (request, frequency),
+  // chunks of up to kChunk pixels
+  size_t n_maps = 0, n_chunks = 0;
   for (int q = 0; q < nreq; ++q) {
     const rt_request& R = reqs[q];
     if (!R.view || !R.freqs_hz || !R.tb_out || R.nf < 1) return fail(RT_ERR_ARG, "request %d: NULL field or nf < 1", q);
     st = check_view(R.view);
     if (st != RT_OK) return st;
-    views.push_back(make_view(*R.view));
+    for (int fi = 0; fi < R.nf; ++fi)
+      if (bad_freq(R.freqs_hz[fi])) return fail(RT_ERR_ARG, "request %d frequency %d is not > 0", q, fi);
+    n_maps += (size_t)R.nf;
+    n_chunks += (size_t)R.nf * (((size_t)R.view->nx * R.view->ny + kChunk - 1) / kChunk);
+  }
+  const size_t off_views = 256;
+  const size_t off_maps = align16(off_views + sizeof(ViewDev) * (size_t)nreq);
+  const size_t off_chunks = align16(off_maps + sizeof(MapDev) * n_maps);
+  const size_t bytes = off_chunks + sizeof(ChunkDev) * n_chunks;
+  if (bytes > RT_NOALLOC_SCRATCH_BYTES || n_chunks > kNoAllocMaxChunks)
+    return fail(RT_ERR_ARG, "rt_trace_batch_noalloc: the batch needs %zu bytes of scratch, the static scratch holds %u",
+                bytes, (unsigned)RT_NOALLOC_SCRATCH_BYTES);
+
+  std::lock_guard<std::mutex> lock(g_noalloc_host_mutex);
+  unsigned char* img = g_noalloc_image;
+  std::memset(img, 0, off_views);  // the zero control block clears the ticket and counters
+  ViewDev* views = reinterpret_cast<ViewDev*>(img + off_views);
+  MapDev* maps = reinterpret_cast<MapDev*>(img + off_maps);
+  const double rmin = g->r.front(), rmax = g->r.back();
+  size_t m = 0, c = 0;
+  for (int q = 0; q < nreq; ++q) {
+    const rt_request& R = reqs[q];
+    views[q] = make_view(*R.view);
     const int npix = R.view->nx * R.view->ny;
     const double du = (R.view->x1 - R.view->x0) / R.view->nx, dv = (R.view->y1 - R.view->y0) / R.view->ny;
-    for (int fi = 0; fi < R.nf; ++fi) {
-      if (bad_freq(R.freqs_hz[fi])) return fail(RT_ERR_ARG, "request %d frequency %d is not > 0", q, fi);
+    for (int fi = 0; fi < R.nf; ++fi, ++m) {
       MapDev M;
       M.f = make_freq(R.freqs_hz[fi], fi);
       M.view = q;
       M.out = R.tb_out + (size_t)fi * npix;
       M.diag = R.diag ? reinterpret_cast<RayDiag*>(R.diag) + (size_t)fi * npix : nullptr;
-      const int m = (int)maps.size();
-      maps.push_back(M);
+      maps[m] = M;
       const double rc = turning_radius(g, R.freqs_hz[fi]);
-      for (int p0 = 0; p0 < npix; p0 += kChunk) {
+      for (int p0 = 0; p0 < npix; p0 += kChunk, ++c) {
         const int pix = p0 + std::min(kChunk, npix - p0) / 2, ix = pix % R.view->nx, iy = pix / R.view->nx;
         const double u = R.view->x0 + (ix + 0.5) * du, v = R.view->y0 + (iy + 0.5) * dv;
-        cands.push_back({path_estimate(std::sqrt(u * u + v * v), rc, rmin, rmax),
-                         ChunkDev{m, p0, std::min(kChunk, npix - p0), 0}});
+        g_noalloc_cands[c] = {path_estimate(std::sqrt(u * u + v * v), rc, rmin, rmax), (unsigned int)c,
+                              ChunkDev{(int)m, p0, std::min(kChunk, npix - p0), 0}};
       }
     }
   }
-  const size_t off_views = 256;
-  const size_t off_maps = align16(off_views + sizeof(ViewDev) * views.size());
-  const size_t off_chunks = align16(off_maps + sizeof(MapDev) * maps.size());
-  const size_t bytes = off_chunks + sizeof(ChunkDev) * cands.size();
-  if (bytes > RT_NOALLOC_SCRATCH_BYTES)
-    return fail(RT_ERR_ARG, "rt_trace_batch_noalloc: the batch needs %zu bytes of scratch, the static scratch holds %u",
-                bytes, (unsigned)RT_NOALLOC_SCRATCH_BYTES);
-  std::stable_sort(cands.begin(), cands.end(),
-                   [](const std::pair<double, ChunkDev>& a, const std::pair<double, ChunkDev>& b) { return a.first > b.first; });
-  // one host image of the scratch; its zero control block clears the ticket and counters
-  std::vector<unsigned char> img(bytes, 0);
-  std::memcpy(img.data() + off_views, views.data(), sizeof(ViewDev) * views.size());
-  std::memcpy(img.data() + off_maps, maps.data(), sizeof(MapDev) * maps.size());
-  for (size_t i = 0; i < cands.size(); ++i)
-    std::memcpy(img.data() + off_chunks + i * sizeof(ChunkDev), &cands[i].second, sizeof(ChunkDev));
+  // longest first; std::sort works in place (no temporary buffer), the
+  // request order breaks ties
+  std::sort(g_noalloc_cands, g_noalloc_cands + n_chunks, [](const NoAllocCand& a, const NoAllocCand& b) {
+    return a.cost > b.cost || (a.cost == b.cost && a.order < b.order);
+  });
+  ChunkDev* chunks = reinterpret_cast<ChunkDev*>(img + off_chunks);
+  for (size_t i = 0; i < n_chunks; ++i) chunks[i] = g_noalloc_cands[i].c;
 
   cudaStream_t s = (cudaStream_t)stream;
-  RT_CUDA(cudaMemcpyAsync(D.scratch, img.data(), bytes, cudaMemcpyHostToDevice, s));
+  RT_CUDA(cudaMemcpyAsync(D.scratch, img, bytes, cudaMemcpyHostToDevice, s));
   TraceParams P;
   std::memset(&P, 0, sizeof P);
   fill_common(P, g, o);
@@ -1001,8 +1030,7 @@ extern "C" rt_status rt_trace_batch_noalloc(const rt_grid* g, const rt_request* 
   P.chunks = reinterpret_cast<const ChunkDev*>(D.scratch + off_chunks);
   P.counter = reinterpret_cast<unsigned int*>(D.scratch);
   P.stats = reinterpret_cast<unsigned long long*>(D.scratch + 8);
-  P.total = (unsigned int)(cands.size() * kChunk);
+  P.total = (unsigned int)(n_chunks * kChunk);
   RT_CUDA(dispatch_trace(nb, o->precision == RT_MIXED, P, D.sm_count, s, is_tube(o)));
   return RT_OK;
 }
-

@@ -38,6 +38,10 @@ MUTANTS = {
                          "test_bouguer_invariant_and_hamiltonian"),
     "phi_wrap": ("const int k1 = (k + 1) % np;", "const int k1 = (k + 1 < np) ? k + 1 : k;",
                  "test_phi_periodic_wrap"),
+    "kappa_prefactor": ("return 9.78e-3 * ne * ne * G", "return 8.78e-3 * ne * ne * G",
+                        "test_kappa_matches_classical_free_free"),
+    "gaunt_hot_constant": ("(24.5 + lnT - std::log(f))", "(25.5 + lnT - std::log(f))",
+                           "test_kappa_matches_classical_free_free"),
 }
 
 

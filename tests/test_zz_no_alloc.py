@@ -1,11 +1,11 @@
 """The allocation-free batch entry point (rt_trace_batch_noalloc).
 
-It serves callers that must not allocate device memory while they trace: a
-stream being captured into a CUDA graph, where cudaMalloc is not allowed, a
-real-time loop on a fixed memory budget, or a host whose device memory is
-owned by another allocator.  Its scratch lives in a static device array of
-the library instead.  This file is collected last so that a run stopping at
-the first failure has already run every other test.
+It serves callers that cannot allocate device memory when they trace: a
+real-time loop that must not stall on cudaMalloc or runs on a memory budget
+fixed at start-up, or a host whose device memory is owned by another
+allocator.  Its scratch lives in a static device array of the library
+instead.  This file is collected last so that a run stopping at the first
+failure has already run every other test.
 """
 import ctypes as C
 
@@ -55,10 +55,8 @@ def test_noalloc_batch_matches_trace_batch_twice():
         rc = L.rt_trace_batch_noalloc(grid.handle, arr, len(reqs), C.byref(opts), stream)
         assert rc == 0, L.rt_last_error()
         torch.cuda.synchronize()
-        for a, b in zip(outs, ref_out):
-            a, b = a.cpu().numpy(), b.cpu().numpy()
-            scale = np.maximum(b, 1e-2 * max(b.max(), 1e-30))
-            assert (np.abs(a - b) <= 1e-3 * scale).all(), f"call {call}"
+        for a, b in zip(outs, ref_out):  # the same rays with the same arithmetic: identical maps
+            assert torch.equal(a, b), f"call {call}"
 
     # a batch larger than the static scratch is refused with a clear error
     big = [cs.Request(cs.View(0.0, 0.0, 2048, 2048, -2.5, 2.5, -2.5, 2.5), np.array([1e8] * 8))]
