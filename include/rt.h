@@ -193,6 +193,23 @@ typedef struct rt_batch_plan rt_batch_plan;
  * RT_ERR_OOM, RT_ERR_CUDA. */
 rt_status rt_batch_plan_create(rt_ctx* ctx, const rt_grid* grid, const rt_request* reqs, int nreq,
                                const rt_options* opt, rt_batch_plan** out);
+/* Multi-GPU partition of one job (the (request, frequency, pixel-chunk)
+ * items of the rays, which are independent, Sec. 3.2): the plan of rank
+ * `rank` of `world_size` holds only the chunks that the longest-first greedy
+ * partition (rt_shard_assign over the plan's path-length estimates) gives
+ * that rank.  Every rank computes the same partition from the same
+ * requests, so the ranks' plans cover every ray exactly once; each rank
+ * writes only its own rays' pixels of the output maps (zero the maps and sum
+ * them over the ranks to gather them).  Per-ray arithmetic is that of
+ * rt_batch_plan_create.  Errors: as rt_batch_plan_create, and RT_ERR_ARG for
+ * rank outside [0, world_size). */
+rt_status rt_batch_plan_create_shard(rt_ctx* ctx, const rt_grid* grid, const rt_request* reqs, int nreq,
+                                     const rt_options* opt, int rank, int world_size, rt_batch_plan** out);
+/* The partition above, on the host (needs no GPU): items are taken in order
+ * of decreasing cost (stable), each given to the rank with the least total
+ * cost so far (the lowest rank on ties).  cost: host [n], finite, >= 0;
+ * rank_of: host [n], written.  Errors: RT_ERR_ARG. */
+rt_status rt_shard_assign(const double* cost, long n, int world_size, int* rank_of);
 /* Replays the plan's graph on `stream` (asynchronous). */
 rt_status rt_batch_plan_launch(rt_batch_plan* plan, void* stream);
 /* Counters of the plan's most recent launch (waits for `stream`). */
@@ -264,6 +281,19 @@ rt_status rt_backward(rt_ctx* ctx, const rt_grid* grid, const rt_view* view, con
 #define RT_NOALLOC_SCRATCH_BYTES (2u << 20)
 rt_status rt_trace_batch_noalloc(const rt_grid* grid, const rt_request* reqs, int nreq,
                                  const rt_options* opt, void* stream);
+
+/* Disk-mean brightness temperature spectrum (Sec. 3.4, Fig. 10: the mean
+ * T_b within 0.5 R_sun of disk centre at each frequency).  For each of the nf
+ * maps of tb, the mean over the pixels whose centre (u, v) (the pixel
+ * mapping of rt_view) satisfies u^2 + v^2 < radius^2; 0 where no pixel
+ * centre lies inside.  Sums in FP64, in a fixed order.
+ * view:     host; the view the maps were traced with (its nx, ny and extent).
+ * tb:       device [nf][ny][nx] float (as written by rt_trace_image).
+ * radius:   > 0, in R_sun.
+ * mean_out: device double [nf], caller-owned.
+ * Asynchronous on `stream`.  Errors: RT_ERR_ARG, RT_ERR_CUDA. */
+rt_status rt_disk_mean_tb(const rt_view* view, const float* tb, int nf, double radius, double* mean_out,
+                          void* stream);
 
 /* Samples the interpolated corona at n points: the field evaluation of
  * every RK4 stage (trilinear n_e, T_e in (r, theta, phi) and the exact

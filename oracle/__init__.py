@@ -267,3 +267,18 @@ def backward(field: FieldHandle, view, freqs, dL_dTb, opts: Options | None = Non
         raise ValueError("orc_backward rejected its arguments")
     shp = (s.n_r, s.n_t, s.n_p)
     return gne.reshape(shp), gte.reshape(shp), tb.reshape(len(freqs), npix)
+
+
+def disk_mean_tb(view, tb, radius=0.5):
+    """Mean brightness temperature within ``radius`` R_sun of disk centre, per
+    frequency (Sec. 3.4: the near-centre quiet-Sun spectrum of Fig. 10): for
+    tb [nf, ny, nx] traced with ``view``, the plain mean over the pixels whose
+    centre (u, v) satisfies u^2 + v^2 < radius^2 (0 if none does)."""
+    tb = np.asarray(tb, dtype=np.float64).reshape(-1, view.ny, view.nx)
+    u = view.x0 + (np.arange(view.nx) + 0.5) * ((view.x1 - view.x0) / view.nx)
+    v = view.y0 + (np.arange(view.ny) + 0.5) * ((view.y1 - view.y0) / view.ny)
+    inside = (u[None, :] ** 2 + v[:, None] ** 2) < radius * radius
+    if not inside.any():
+        return np.zeros(tb.shape[0])
+    return np.array([m[inside].mean() for m in tb])
+

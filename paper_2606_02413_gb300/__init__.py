@@ -220,6 +220,20 @@ class Context:
                                 _stream_ptr(stream)), "rt_backward")
         return (dne, dte, tb) if want_tb else (dne, dte)
 
+    def disk_mean_tb(self, v, tb, radius=0.5, stream=None):
+        """rt_disk_mean_tb: the mean T_b within `radius` R_sun of disk centre of
+        each map in tb (a [nf, ny, nx] float32 CUDA tensor traced with view v).
+        Returns a float64 CUDA tensor [nf]."""
+        import torch
+        vs = view(v)
+        assert tb.is_cuda and tb.dtype == torch.float32 and tb.is_contiguous()
+        nf = tb.numel() // (vs.nx * vs.ny)
+        assert nf * vs.nx * vs.ny == tb.numel()
+        out = torch.empty(nf, dtype=torch.float64, device=tb.device)
+        check(lib().rt_disk_mean_tb(C.byref(vs), C.c_void_p(tb.data_ptr()), nf, float(radius),
+                                    C.c_void_p(out.data_ptr()), _stream_ptr(stream)), "rt_disk_mean_tb")
+        return out
+
     def probe_field(self, grid: Grid, xyz, stream=None):
         """rt_probe_field: (n_e, T_e, grad n_e) at points xyz [n, 3] -> [n, 5]."""
         import torch

@@ -22,9 +22,10 @@ RAY_STATUS = {1: "EXIT_OUTER", 2: "HIT_INNER", 3: "TAU_STOP", 4: "STEP_LIMIT", 5
 
 # every symbol include/rt.h declares
 EXPORTS = ["rt_default_options", "rt_status_string", "rt_last_error", "rt_create", "rt_destroy",
-           "rt_load_grid", "rt_free_grid", "rt_trace_image", "rt_backward", "rt_batch_plan_create", "rt_batch_plan_launch",
+           "rt_load_grid", "rt_free_grid", "rt_trace_image", "rt_backward", "rt_batch_plan_create",
+           "rt_batch_plan_create_shard", "rt_shard_assign", "rt_batch_plan_launch",
            "rt_batch_plan_stats", "rt_batch_plan_destroy", "rt_trace_batch", "rt_trace_batch_noalloc",
-           "rt_probe_field", "rt_sync", "rt_get_stats"]
+           "rt_probe_field", "rt_disk_mean_tb", "rt_sync", "rt_get_stats"]
 
 
 class GridDesc(C.Structure):
@@ -96,17 +97,22 @@ def lib():
         L.rt_backward.argtypes = [vp, vp, C.POINTER(View), C.POINTER(C.c_double), ip, C.POINTER(Options),
                                   vp, vp, vp, vp, vp, vp]
         L.rt_batch_plan_create.argtypes = [vp, vp, C.POINTER(Request), ip, C.POINTER(Options), C.POINTER(vp)]
+        L.rt_batch_plan_create_shard.argtypes = [vp, vp, C.POINTER(Request), ip, C.POINTER(Options), ip, ip,
+                                                 C.POINTER(vp)]
+        L.rt_shard_assign.argtypes = [C.POINTER(C.c_double), C.c_long, ip, C.POINTER(C.c_int)]
         L.rt_batch_plan_launch.argtypes = [vp, vp]
         L.rt_batch_plan_stats.argtypes = [vp, vp, C.POINTER(Stats)]
         L.rt_batch_plan_destroy.argtypes = [vp]
         L.rt_trace_batch.argtypes = [vp, vp, C.POINTER(Request), ip, C.POINTER(Options), vp]
         L.rt_trace_batch_noalloc.argtypes = [vp, C.POINTER(Request), ip, C.POINTER(Options), vp]
+        L.rt_disk_mean_tb.argtypes = [C.POINTER(View), vp, ip, C.c_double, vp, vp]
         L.rt_sync.argtypes = [vp, vp]
         L.rt_get_stats.argtypes = [vp, vp, C.POINTER(Stats)]
         for name in ("rt_create", "rt_destroy", "rt_load_grid", "rt_free_grid", "rt_trace_image", "rt_backward",
-                     "rt_batch_plan_create", "rt_batch_plan_launch", "rt_batch_plan_stats",
+                     "rt_batch_plan_create", "rt_batch_plan_create_shard", "rt_shard_assign",
+                     "rt_batch_plan_launch", "rt_batch_plan_stats",
                      "rt_batch_plan_destroy", "rt_trace_batch", "rt_trace_batch_noalloc", "rt_probe_field",
-                     "rt_sync", "rt_get_stats"):
+                     "rt_disk_mean_tb", "rt_sync", "rt_get_stats"):
             getattr(L, name).restype = ip
         _lib = L
         return _lib

@@ -53,11 +53,8 @@ __device__ __forceinline__ CellGeom cell_geom(const GridDev& G, float x, float y
     c.inv_r = c.rho = c.inv_rho = 0.f;
     return c;
   }
-  int bin = __float2int_rd((r - G.r_lut0) * G.r_lut_inv);
-  bin = min(max(bin, 0), G.r_lut_n - 1);
-  const int2 e = __ldg(G.r_lut + bin);
-  c.i = min(e.x + (r >= __int_as_float(e.y) ? 1 : 0), G.n_r - 2);
-  const float2 rc = __ldg(G.r_cell + c.i);
+  float2 rc;
+  c.i = radial_lookup(G, r, rc.x, rc.y);
   c.u = (r - rc.x) * rc.y;
   const float inv_rho = (rho2 > 0.f) ? rsqrtf(rho2) : 0.f;
   const float rho = rho2 * inv_rho;

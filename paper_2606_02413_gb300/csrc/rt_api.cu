@@ -13,6 +13,7 @@
 
 #include "rt.h"
 #include "rt_adjoint.cuh"
+#include "rt_rays.cuh"
 
 using namespace rt;
 
@@ -48,12 +49,6 @@ rt_status fail(rt_status code, const char* fmt, ...) {
 
 double c_pe() { return kElectronCharge * kElectronCharge / (kPi * kElectronMass); }
 
-int float_bits(float f) {
-  int i;
-  std::memcpy(&i, &f, sizeof i);
-  return i;
-}
-
 }  // namespace
 
 struct rt_ctx {
@@ -68,7 +63,7 @@ struct rt_grid {
   int device = 0;                // CUDA device that holds the grid
   float4* ne = nullptr;
   float4* te = nullptr;
-  int2* lut = nullptr;
+  RadBin* lut = nullptr;
   float2* rcell = nullptr;
   int n_r = 0, n_t = 0, n_p = 0;
   std::vector<double> r;         // radial nodes
@@ -154,6 +149,39 @@ __global__ void probe_field(const GridDev G, const float* __restrict__ xyz, int 
   out[5 * i + 4] = s.gz;
 }
 
+// Mean T_b over the pixels whose centre lies within `radius` of the image
+// centre (Sec. 3.4: the near-centre quiet-Sun spectrum); one block per
+// frequency, FP64 sums in a fixed order (deterministic).
+constexpr int kDiskThreads = 512;
+__global__ void __launch_bounds__(kDiskThreads) disk_mean(const float* __restrict__ tb, int nx, int ny, double x0,
+                                                          double dx, double y0, double dy, double r2,
+                                                          double* __restrict__ out) {
+  __shared__ double sum[kDiskThreads];
+  __shared__ long long cnt[kDiskThreads];
+  const float* map = tb + (size_t)blockIdx.x * nx * ny;
+  double s = 0.0;
+  long long c = 0;
+  for (long p = threadIdx.x; p < (long)nx * ny; p += kDiskThreads) {
+    const int ix = (int)(p % nx), iy = (int)(p / nx);
+    const double u = x0 + (ix + 0.5) * dx, v = y0 + (iy + 0.5) * dy;
+    if (u * u + v * v < r2) {
+      s += (double)map[p];
+      c += 1;
+    }
+  }
+  sum[threadIdx.x] = s;
+  cnt[threadIdx.x] = c;
+  __syncthreads();
+  for (int w = kDiskThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sum[threadIdx.x] += sum[threadIdx.x + w];
+      cnt[threadIdx.x] += cnt[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = cnt[0] > 0 ? sum[0] / (double)cnt[0] : 0.0;
+}
+
 template <int NB, bool M, bool T>
 int blocks_per_sm() {
   static int cached = -1;
@@ -177,31 +205,52 @@ int adj_blocks_per_sm() {
   return cached;
 }
 
-template <int NB, bool M, bool T>
-cudaError_t launch_trace(const TraceParams& P, int sm_count, cudaStream_t s) {
-  const int fit = blocks_per_sm<NB, M, T>();
+template <int NB, bool M>
+int ray_blocks_per_sm() {
+  static int cached = -1;
+  if (cached < 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_rays<NB, M>, kThreads, 0) != cudaSuccess || b < 1)
+      b = 1;
+    cached = b;
+  }
+  return cached;
+}
+
+// tube mode: the lane-parallel bundle kernel (persistent neighbours)
+template <int NB, bool M>
+cudaError_t launch_tube(const TraceParams& P, int sm_count, cudaStream_t s) {
+  const int fit = blocks_per_sm<NB, M, true>();
   const int per_sm = (P.blocks_per_sm > 0) ? std::min(P.blocks_per_sm, fit) : fit;
-  const int grid = sm_count * per_sm;
-  trace_bundles<NB, M, T><<<grid, kThreads, 0, s>>>(P);
+  trace_bundles<NB, M, true><<<sm_count * per_sm, kThreads, 0, s>>>(P);
   return cudaGetLastError();
 }
 
-// nb: neighbour lanes per bundle (0 = magnification off); tube: persistent
+// step-wise magnification (or none): one thread per bundle
+template <int NB, bool M>
+cudaError_t launch_rays(const TraceParams& P, int sm_count, cudaStream_t s) {
+  const int fit = ray_blocks_per_sm<NB, M>();
+  const int per_sm = (P.blocks_per_sm > 0) ? std::min(P.blocks_per_sm, fit) : fit;
+  trace_rays<NB, M><<<sm_count * per_sm, kThreads, 0, s>>>(P);
+  return cudaGetLastError();
+}
+
+// nb: neighbour rays per bundle (0 = magnification off); tube: persistent
 // neighbours (tube mode) instead of the step-wise retrace
 cudaError_t dispatch_trace(int nb, bool mixed, const TraceParams& P, int sm, cudaStream_t s, bool tube = false) {
   if (tube) {
     switch (nb) {
-      case 2: return mixed ? launch_trace<2, true, true>(P, sm, s) : launch_trace<2, false, true>(P, sm, s);
-      case 4: return mixed ? launch_trace<4, true, true>(P, sm, s) : launch_trace<4, false, true>(P, sm, s);
-      case 8: return mixed ? launch_trace<8, true, true>(P, sm, s) : launch_trace<8, false, true>(P, sm, s);
+      case 2: return mixed ? launch_tube<2, true>(P, sm, s) : launch_tube<2, false>(P, sm, s);
+      case 4: return mixed ? launch_tube<4, true>(P, sm, s) : launch_tube<4, false>(P, sm, s);
+      case 8: return mixed ? launch_tube<8, true>(P, sm, s) : launch_tube<8, false>(P, sm, s);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (nb) {
-    case 0: return mixed ? launch_trace<0, true, false>(P, sm, s) : launch_trace<0, false, false>(P, sm, s);
-    case 2: return mixed ? launch_trace<2, true, false>(P, sm, s) : launch_trace<2, false, false>(P, sm, s);
-    case 4: return mixed ? launch_trace<4, true, false>(P, sm, s) : launch_trace<4, false, false>(P, sm, s);
-    case 8: return mixed ? launch_trace<8, true, false>(P, sm, s) : launch_trace<8, false, false>(P, sm, s);
+    case 0: return mixed ? launch_rays<0, true>(P, sm, s) : launch_rays<0, false>(P, sm, s);
+    case 2: return mixed ? launch_rays<2, true>(P, sm, s) : launch_rays<2, false>(P, sm, s);
+    case 4: return mixed ? launch_rays<4, true>(P, sm, s) : launch_rays<4, false>(P, sm, s);
+    case 8: return mixed ? launch_rays<8, true>(P, sm, s) : launch_rays<8, false>(P, sm, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -320,19 +369,27 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
   if (nb_d > (double)(1 << 22)) return fail(RT_ERR_GRID, "rt_load_grid: radial spacing too uneven for the lookup table");
   const int nb = (int)nb_d;
   const double bw = span / nb;
-  std::vector<int2> lut(nb);
+  std::vector<float2> rcell(nr - 1);
+  for (int i = 0; i + 1 < nr; ++i)
+    rcell[i] = make_float2(Rf[i], (float)(1.0 / ((double)Rf[i + 1] - (double)Rf[i])));
+  std::vector<RadBin> lut(nb);
   for (int b = 0; b < nb; ++b) {
     const double lo = (double)Rf[0] + b * bw, hi = lo + bw;
     int base = (int)(std::upper_bound(Rf.begin(), Rf.end(), (float)lo) - Rf.begin()) - 1;
     base = std::min(std::max(base, 0), nr - 2);
     while (base > 0 && (double)Rf[base] > lo) --base;
-    float split = std::numeric_limits<float>::infinity();
-    if (base + 1 <= nr - 2 && (double)Rf[base + 1] < hi) split = Rf[base + 1];
-    lut[b] = make_int2(base, float_bits(split));
+    RadBin e{};
+    e.base = base;
+    e.split = std::numeric_limits<float>::infinity();
+    e.r0 = rcell[base].x;
+    e.inv0 = rcell[base].y;
+    e.inv1 = 0.f;
+    if (base + 1 <= nr - 2 && (double)Rf[base + 1] < hi) {
+      e.split = Rf[base + 1];
+      e.inv1 = rcell[base + 1].y;
+    }
+    lut[b] = e;
   }
-  std::vector<float2> rcell(nr - 1);
-  for (int i = 0; i + 1 < nr; ++i)
-    rcell[i] = make_float2(Rf[i], (float)(1.0 / ((double)Rf[i + 1] - (double)Rf[i])));
 
   RT_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
@@ -363,7 +420,7 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&g->ne, sizeof(float4) * 2 * ncell);
   if (e == cudaSuccess) e = cudaMalloc(&g->te, sizeof(float4) * 2 * ncell);
-  if (e == cudaSuccess) e = cudaMalloc(&g->lut, sizeof(int2) * nb);
+  if (e == cudaSuccess) e = cudaMalloc(&g->lut, sizeof(RadBin) * nb);
   if (e == cudaSuccess) e = cudaMalloc(&g->rcell, sizeof(float2) * (nr - 1));
   if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&d_shell, sizeof(double) * nr);
@@ -383,7 +440,7 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
     src_ne = tmp_ne;
     src_te = tmp_te;
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(g->lut, lut.data(), sizeof(int2) * nb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->lut, lut.data(), sizeof(RadBin) * nb, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(g->rcell, rcell.data(), sizeof(float2) * (nr - 1), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned int), s);
   const int blocks = ctx->sm_count * 8;
@@ -417,7 +474,7 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
   GridDev& G = g->dev;
   G.ne = g->ne;
   G.te = g->te;
-  G.r_lut = g->lut;
+  G.r_bins = g->lut;
   G.r_cell = g->rcell;
   G.n_r = nr; G.n_t = nt; G.n_p = np;
   G.r_lut_n = nb;
@@ -616,11 +673,33 @@ rt_status rt_batch_plan_destroy(rt_batch_plan* p) {
   return RT_OK;
 }
 
-rt_status rt_batch_plan_create(rt_ctx* ctx, const rt_grid* g, const rt_request* reqs, int nreq,
-                               const rt_options* o, rt_batch_plan** out) {
+rt_status rt_shard_assign(const double* cost, long n, int world_size, int* rank_of) {
+  if (n < 0 || (n > 0 && (!cost || !rank_of))) return fail(RT_ERR_ARG, "rt_shard_assign: bad arguments");
+  if (world_size < 1) return fail(RT_ERR_ARG, "rt_shard_assign: world_size = %d", world_size);
+  std::vector<long> order((size_t)n);
+  for (long i = 0; i < n; ++i) {
+    if (!(cost[i] >= 0.0) || !std::isfinite(cost[i])) return fail(RT_ERR_ARG, "rt_shard_assign: cost %ld", i);
+    order[(size_t)i] = i;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](long a, long b) { return cost[a] > cost[b]; });
+  std::vector<double> load((size_t)world_size, 0.0);
+  for (long i : order) {
+    int best = 0;
+    for (int r = 1; r < world_size; ++r)
+      if (load[(size_t)r] < load[(size_t)best]) best = r;
+    rank_of[i] = best;
+    load[(size_t)best] += cost[i];
+  }
+  return RT_OK;
+}
+
+static rt_status plan_create(rt_ctx* ctx, const rt_grid* g, const rt_request* reqs, int nreq, const rt_options* o,
+                             int rank, int world_size, rt_batch_plan** out) {
   if (!ctx || !g || !reqs || !out) return fail(RT_ERR_ARG, "rt_batch_plan_create: NULL argument");
   *out = nullptr;
   if (nreq < 1) return fail(RT_ERR_ARG, "rt_batch_plan_create: nreq = %d", nreq);
+  if (world_size < 1 || rank < 0 || rank >= world_size)
+    return fail(RT_ERR_ARG, "rt_batch_plan_create: rank %d of %d", rank, world_size);
   int nb = 0;
   rt_status st = check_options(o, &nb);
   if (st != RT_OK) return st;
@@ -661,13 +740,25 @@ rt_status rt_batch_plan_create(rt_ctx* ctx, const rt_grid* g, const rt_request* 
   }
   if ((double)cands.size() * kChunk >= 4.0e9) return fail(RT_ERR_ARG, "rt_batch_plan_create: too many rays");
   std::stable_sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) { return a.cost > b.cost; });
-  std::vector<ChunkDev> chunks(cands.size());
-  for (size_t i = 0; i < cands.size(); ++i) chunks[i] = cands[i].c;
+  std::vector<ChunkDev> chunks;
+  if (world_size == 1) {
+    chunks.resize(cands.size());
+    for (size_t i = 0; i < cands.size(); ++i) chunks[i] = cands[i].c;
+  } else {  // this rank's share of the longest-first greedy partition (same on every rank)
+    std::vector<double> cost(cands.size());
+    std::vector<int> owner(cands.size());
+    for (size_t i = 0; i < cands.size(); ++i) cost[i] = cands[i].cost;
+    st = rt_shard_assign(cost.data(), (long)cands.size(), world_size, owner.data());
+    if (st != RT_OK) return st;
+    for (size_t i = 0; i < cands.size(); ++i)
+      if (owner[i] == rank) chunks.push_back(cands[i].c);
+  }
+  const size_t n_alloc = std::max<size_t>(chunks.size(), 1);
 
   RT_CUDA(cudaSetDevice(ctx->device));
   rt_batch_plan* p = new rt_batch_plan;
   p->ctx = ctx;
-  cudaError_t e = cudaMalloc(&p->chunks, sizeof(ChunkDev) * chunks.size());
+  cudaError_t e = cudaMalloc(&p->chunks, sizeof(ChunkDev) * n_alloc);
   if (e == cudaSuccess) e = cudaMalloc(&p->maps, sizeof(MapDev) * maps.size());
   if (e == cudaSuccess) e = cudaMalloc(&p->views, sizeof(ViewDev) * views.size());
   if (e == cudaSuccess) e = cudaMalloc(&p->counter, 64);
@@ -702,6 +793,16 @@ rt_status rt_batch_plan_create(rt_ctx* ctx, const rt_grid* g, const rt_request* 
   }
   *out = p;
   return RT_OK;
+}
+
+rt_status rt_batch_plan_create(rt_ctx* ctx, const rt_grid* g, const rt_request* reqs, int nreq,
+                               const rt_options* o, rt_batch_plan** out) {
+  return plan_create(ctx, g, reqs, nreq, o, 0, 1, out);
+}
+
+rt_status rt_batch_plan_create_shard(rt_ctx* ctx, const rt_grid* g, const rt_request* reqs, int nreq,
+                                     const rt_options* o, int rank, int world_size, rt_batch_plan** out) {
+  return plan_create(ctx, g, reqs, nreq, o, rank, world_size, out);
 }
 
 rt_status rt_batch_plan_launch(rt_batch_plan* p, void* stream) {
@@ -869,6 +970,18 @@ rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const dou
   if (mismatch)
     return fail(RT_ERR_ARG, "rt_backward: fwd_diag does not match this forward (%llu rays with other step counts)",
                 mismatch);
+  return RT_OK;
+}
+
+rt_status rt_disk_mean_tb(const rt_view* v, const float* tb, int nf, double radius, double* mean_out, void* stream) {
+  if (!tb || !mean_out) return fail(RT_ERR_ARG, "rt_disk_mean_tb: NULL argument");
+  rt_status st = check_view(v);
+  if (st != RT_OK) return st;
+  if (nf < 1) return fail(RT_ERR_ARG, "rt_disk_mean_tb: nf = %d", nf);
+  if (!(radius > 0.0) || !std::isfinite(radius)) return fail(RT_ERR_ARG, "rt_disk_mean_tb: radius must be > 0");
+  disk_mean<<<nf, kDiskThreads, 0, (cudaStream_t)stream>>>(tb, v->nx, v->ny, v->x0, (v->x1 - v->x0) / v->nx, v->y0,
+                                                          (v->y1 - v->y0) / v->ny, radius * radius, mean_out);
+  RT_CUDA(cudaGetLastError());
   return RT_OK;
 }
 

@@ -71,6 +71,86 @@ __device__ __forceinline__ float chord_crossing(const Vec& r, const Vec& dr, flo
   return fminf(a, 1.f);
 }
 
+// A ticket decoded into its ray (Sec. 3.2): the view, frequency, pixel and
+// outputs, and the launch state.  valid = false for a ticket past a ragged
+// chunk or tile edge (no ray behind it); enter = false for a MISS (the line
+// misses the outer sphere, or n^2 <= 0 at the entry point).
+struct RayStart {
+  const ViewDev* V;
+  const FreqDev* F;
+  float* out;
+  RayDiag* dg;
+  bool valid, enter;
+  float px, py, pz, kx, ky, kz;  // entry point on the outer sphere, k = n(r0) (-o)
+  float u, v, sc, nc, nec;       // image-plane point, entry depth, n and n_e at the entry (tube launch)
+};
+
+__device__ __forceinline__ RayStart start_ray(const TraceParams& P, unsigned int item) {
+  RayStart s;
+  int pix;
+  s.valid = true;
+  if (P.chunks) {
+    const ChunkDev c = P.chunks[item >> kChunkShift];
+    const int off = (int)(item & (kChunk - 1));
+    s.valid = off < c.count;
+    const MapDev& M = P.maps[c.map];
+    pix = c.pix0 + off;
+    s.V = &P.views[M.view];
+    s.F = &M.f;
+    s.out = M.out + pix;
+    s.dg = M.diag ? M.diag + pix : nullptr;
+  } else {
+    const int fi = item / P.view.tickets;
+    const int t = item - fi * P.view.tickets;
+    if (P.view.tile > 0) {  // tile-major walk; tickets past the image edge carry no ray
+      const int T = P.view.tile, tt = T * T;
+      const int tile = t / tt, w = t - tile * tt;
+      const int ix = (tile % P.view.tiles_x) * T + w % T, iy = (tile / P.view.tiles_x) * T + w / T;
+      s.valid = ix < P.view.nx && iy < P.view.ny;
+      pix = s.valid ? iy * P.view.nx + ix : 0;
+    } else {
+      pix = t;
+    }
+    s.V = &P.view;
+    s.F = &P.freq[fi];
+    const size_t o = (size_t)s.F->out_slab * P.view.npix + pix;
+    s.out = P.tb_out + o;
+    s.dg = P.diag ? P.diag + o : nullptr;
+  }
+  s.enter = false;
+  s.px = s.py = s.pz = s.kx = s.ky = s.kz = 0.f;
+  s.u = s.v = s.sc = s.nec = 0.f;
+  s.nc = 1.f;
+  if (!s.valid) return s;
+  const ViewDev* V = s.V;
+  const int ix = pix % V->nx, iy = pix / V->nx;
+  s.u = fmaf((float)ix + 0.5f, V->dx, V->x0);
+  s.v = fmaf((float)iy + 0.5f, V->dy, V->y0);
+  const float R = P.G.r_max;
+  const float b2 = fmaf(s.u, s.u, s.v * s.v);
+  bool ok = b2 < R * R;
+  if (ok) {
+    s.sc = sqrtf(fmaf(R, R, -b2));
+    s.px = fmaf(s.u, V->eux, fmaf(s.v, V->evx, s.sc * V->ox));
+    s.py = fmaf(s.u, V->euy, fmaf(s.v, V->evy, s.sc * V->oy));
+    s.pz = fmaf(s.u, V->euz, fmaf(s.v, V->evz, s.sc * V->oz));
+    if (!P.straight) {
+      const Sample s0 = eval_field(P.G, s.px, s.py, s.pz, false);
+      s.nec = s0.ne;
+      const float n2 = fmaf(s.F->kn2, s0.ne, 1.f);
+      ok = n2 > 0.f;
+      s.nc = ok ? sqrtf(n2) : 0.f;
+    }
+  }
+  s.enter = ok;
+  if (ok) {
+    s.kx = -s.nc * V->ox;
+    s.ky = -s.nc * V->oy;
+    s.kz = -s.nc * V->oz;
+  }
+  return s;
+}
+
 // Per-bundle state of the central lane, kept in shared memory so that only
 // the RK4 state lives in registers across the four field evaluations.
 struct BundleState {
@@ -189,84 +269,32 @@ __global__ void __launch_bounds__(kThreads, kTube ? kMinBlocksTube : kMinBlocks)
           exhausted = true;
           need = false;
         } else {
-          // decode the ticket into (view, frequency, pixel, output)
-          const ViewDev* V;
-          const FreqDev* F;
-          int pix;
-          bool valid = true;
-          if (P.chunks) {
-            const ChunkDev c = P.chunks[item >> kChunkShift];
-            const int off = (int)(item & (kChunk - 1));
-            valid = off < c.count;
-            const MapDev& M = P.maps[c.map];
-            pix = c.pix0 + off;
-            V = &P.views[M.view];
-            F = &M.f;
-            B.out = M.out + pix;
-            B.dg = M.diag ? M.diag + pix : nullptr;
-          } else {
-            const int fi = item / P.view.tickets;
-            const int t = item - fi * P.view.tickets;
-            if (P.view.tile > 0) {  // tile-major walk; tickets past the image edge carry no ray
-              const int T = P.view.tile, tt = T * T;
-              const int tile = t / tt, w = t - tile * tt;
-              const int ix = (tile % P.view.tiles_x) * T + w % T, iy = (tile / P.view.tiles_x) * T + w / T;
-              valid = ix < P.view.nx && iy < P.view.ny;
-              pix = valid ? iy * P.view.nx + ix : 0;
-            } else {
-              pix = t;
-            }
-            V = &P.view;
-            F = &P.freq[fi];
-            const size_t o = (size_t)F->out_slab * P.view.npix + pix;
-            B.out = P.tb_out + o;
-            B.dg = P.diag ? P.diag + o : nullptr;
-          }
-          if (valid) {  // a ragged chunk tail has no ray behind the ticket: take another
-            // launch (Sec. 3.2): entry point on the outer sphere, k = n(r0) (-o)
+          const RayStart rs = start_ray(P, item);
+          B.out = rs.out;
+          B.dg = rs.dg;
+          if (rs.valid) {  // a ragged chunk tail has no ray behind the ticket: take another
             B.item = item;
-            B.kf = P.straight ? 0.f : F->kf;
-            B.kap_c = F->kap_c;
-            B.ln_f = F->ln_f;
+            B.kf = P.straight ? 0.f : rs.F->kf;
+            B.kap_c = rs.F->kap_c;
+            B.ln_f = rs.F->ln_f;
             B.step = 0;
             B.tau_hi = B.tau_lo = B.lns_hi = B.lns_lo = B.tb_hi = B.tb_lo = 0.f;
             B.rl[0] = B.rl[1] = B.rl[2] = B.kl[0] = B.kl[1] = B.kl[2] = 0.f;
             emitted = false;
-            const int ix = pix % V->nx, iy = pix / V->nx;
-            const float u = fmaf((float)ix + 0.5f, V->dx, V->x0);
-            const float v = fmaf((float)iy + 0.5f, V->dy, V->y0);
-            const float R = P.G.r_max;
-            const float b2 = fmaf(u, u, v * v);
-            bool ok = b2 < R * R;
-            float nn = 1.f, ne0 = 0.f;
-            float r0x = 0.f, r0y = 0.f, r0z = 0.f;
-            if (ok) {
-              const float s = sqrtf(fmaf(R, R, -b2));
-              r0x = fmaf(u, V->eux, fmaf(v, V->evx, s * V->ox));
-              r0y = fmaf(u, V->euy, fmaf(v, V->evy, s * V->oy));
-              r0z = fmaf(u, V->euz, fmaf(v, V->evz, s * V->oz));
-              if (!P.straight) {
-                const Sample s0 = eval_field(P.G, r0x, r0y, r0z, false);
-                ne0 = s0.ne;
-                const float n2 = fmaf(F->kn2, s0.ne, 1.f);
-                ok = n2 > 0.f;
-                nn = ok ? sqrtf(n2) : 0.f;
-              }
-            }
-            if (!ok) {
-              finish(kMiss, r0x, r0y, r0z, 0.f);
+            if (!rs.enter) {
+              finish(kMiss, rs.px, rs.py, rs.pz, 0.f);
             } else {
-              px = r0x; py = r0y; pz = r0z;
-              kx = -nn * V->ox; ky = -nn * V->oy; kz = -nn * V->oz;
+              px = rs.px; py = rs.py; pz = rs.pz;
+              kx = rs.kx; ky = rs.ky; kz = rs.kz;
               phase = 1;
               need = false;
               if (kTube) {
-                B.view = V;
-                B.u = u; B.v = v;
-                B.sc = sqrtf(fmaf(R, R, -b2));
-                B.nc = nn;
-                B.nec = ne0;
-                B.kn2 = F->kn2;
+                B.view = rs.V;
+                B.u = rs.u; B.v = rs.v;
+                B.sc = rs.sc;
+                B.nc = rs.nc;
+                B.nec = rs.nec;
+                B.kn2 = rs.F->kn2;
                 fresh = true;
               }
             }

@@ -19,12 +19,27 @@ constexpr int kMinBlocksTube = 6;          // tube bundles: the offset evaluatio
 // ------------------------------------------------------------------ grid
 // Cells are corner-packed: cell (i, j, k) stores the 8 node values of its
 // corners as two float4, corner index a*4 + b*2 + c for the (r, theta, phi)
-// offsets (a, b, c), so one evaluation is two 16-byte loads from one 32-byte
-// sector.  Cell k = n_phi - 1 wraps to node 0 (phi is periodic).
+// offsets (a, b, c), so one evaluation is one 32-byte load of one sector.
+// Cell k = n_phi - 1 wraps to node 0 (phi is periodic).
+//
+// The radial axis (any monotone spacing) is resolved by bins no wider than
+// the narrowest cell, so at most one node lies inside a bin; a bin holds
+// everything one lookup needs in one 32-byte sector: the cell at its lower
+// edge, the node inside it (or +inf), and the base radius and inverse width
+// of the two cells it can select.
+struct __align__(32) RadBin {
+  int base;     // cell at the bin's lower edge
+  float split;  // R_{base+1} when that node lies inside the bin, else +inf
+  float r0;     // R_base
+  float inv0;   // 1 / (R_{base+1} - R_base)
+  float inv1;   // 1 / (R_{base+2} - R_{base+1}) (used only when split is finite)
+  float pad[3];
+};
+
 struct GridDev {
   const float4* ne;      // [cells][2]
   const float4* te;      // [cells][2]
-  const int2* r_lut;     // radial bins: (cell at the bin's lower edge, bits of the node inside the bin or +inf)
+  const RadBin* r_bins;  // [r_lut_n]
   const float2* r_cell;  // [n_r - 1]: (R_i, 1 / (R_{i+1} - R_i))
   int n_r, n_t, n_p;
   int r_lut_n;
@@ -33,6 +48,15 @@ struct GridDev {
   float t0, t_inv, t_last;    // theta_0, 1 / dtheta, n_t - 1
   float p0, p_inv;            // phi_0, n_p / (2 pi)
 };
+
+// One 32-byte load through the read-only path (a 256-bit vector load, sm_100
+// and later); p must be 32-byte aligned.
+__device__ __forceinline__ void ldg8(const void* p, float& v0, float& v1, float& v2, float& v3, float& v4,
+                                     float& v5, float& v6, float& v7) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(v0), "=f"(v1), "=f"(v2), "=f"(v3), "=f"(v4), "=f"(v5), "=f"(v6), "=f"(v7)
+      : "l"(p));
+}
 
 struct Sample {
   float ne, te, gx, gy, gz;  // n_e, T_e, grad n_e
@@ -68,16 +92,17 @@ __device__ __forceinline__ float atan2_grid(float y, float x) {
 // only the T_e loads diverge, the evaluation itself stays warp-uniform).
 // sample_cell does the corner loads, the interpolation and the chain rule
 // for cell (i, j, k) at fractions (u, v, w) of the point (x, y, z).
-__device__ __forceinline__ Sample sample_cell(const GridDev& G, int i, int j, int k, float u, float v, float w,
-                                              float tsel, float inv_dr, float x, float y, float z,
-                                              float inv_r, float rho, float inv_rho, bool want_te) {
+template <bool kTe>
+__device__ __forceinline__ Sample sample_cell_t(const GridDev& G, int i, int j, int k, float u, float v, float w,
+                                                float tsel, float inv_dr, float x, float y, float z, float inv_r,
+                                                float rho, float inv_rho, bool want_te) {
   Sample s;
   const int cell = (i * (G.n_t - 1) + j) * G.n_p + k;
-  const float4 c0 = __ldg(G.ne + 2 * cell);      // (000, 001, 010, 011)
-  const float4 c1 = __ldg(G.ne + 2 * cell + 1);  // (100, 101, 110, 111)
-  const float d00 = c0.y - c0.x, d01 = c0.w - c0.z, d10 = c1.y - c1.x, d11 = c1.w - c1.z;
-  const float a00 = fmaf(w, d00, c0.x), a01 = fmaf(w, d01, c0.z);
-  const float a10 = fmaf(w, d10, c1.x), a11 = fmaf(w, d11, c1.z);
+  float n000, n001, n010, n011, n100, n101, n110, n111;
+  ldg8(G.ne + 2 * cell, n000, n001, n010, n011, n100, n101, n110, n111);
+  const float d00 = n001 - n000, d01 = n011 - n010, d10 = n101 - n100, d11 = n111 - n110;
+  const float a00 = fmaf(w, d00, n000), a01 = fmaf(w, d01, n010);
+  const float a10 = fmaf(w, d10, n100), a11 = fmaf(w, d11, n110);
   const float e0 = a01 - a00, e1 = a11 - a10;
   const float b0 = fmaf(v, e0, a00), b1 = fmaf(v, e1, a10);
   const float fu = b1 - b0;
@@ -98,15 +123,21 @@ __device__ __forceinline__ Sample sample_cell(const GridDev& G, int i, int j, in
   s.gy = fmaf(A + B, y, C * x);
   s.gz = fmaf(A, z, -D);
   s.te = 0.f;
-  if (want_te) {
-    const float4 t0 = __ldg(G.te + 2 * cell);
-    const float4 t1 = __ldg(G.te + 2 * cell + 1);
-    const float p00 = fmaf(w, t0.y - t0.x, t0.x), p01 = fmaf(w, t0.w - t0.z, t0.z);
-    const float p10 = fmaf(w, t1.y - t1.x, t1.x), p11 = fmaf(w, t1.w - t1.z, t1.z);
+  if (kTe && want_te) {
+    float t000, t001, t010, t011, t100, t101, t110, t111;
+    ldg8(G.te + 2 * cell, t000, t001, t010, t011, t100, t101, t110, t111);
+    const float p00 = fmaf(w, t001 - t000, t000), p01 = fmaf(w, t011 - t010, t010);
+    const float p10 = fmaf(w, t101 - t100, t100), p11 = fmaf(w, t111 - t110, t110);
     const float q0 = fmaf(v, p01 - p00, p00), q1 = fmaf(v, p11 - p10, p10);
     s.te = fmaf(u, q1 - q0, q0);
   }
   return s;
+}
+
+__device__ __forceinline__ Sample sample_cell(const GridDev& G, int i, int j, int k, float u, float v, float w,
+                                              float tsel, float inv_dr, float x, float y, float z,
+                                              float inv_r, float rho, float inv_rho, bool want_te) {
+  return sample_cell_t<true>(G, i, j, k, u, v, w, tsel, inv_dr, x, y, z, inv_r, rho, inv_rho, want_te);
 }
 
 __device__ __forceinline__ Sample vacuum_sample() {
@@ -115,23 +146,35 @@ __device__ __forceinline__ Sample vacuum_sample() {
   return s;
 }
 
-// radial cell of r from the lookup table: at most one node lies inside a bin
-__device__ __forceinline__ int radial_cell(const GridDev& G, float r) {
+// Radial cell of r and its base radius and inverse width, from one bin.
+__device__ __forceinline__ int radial_lookup(const GridDev& G, float r, float& R, float& inv) {
   int bin = __float2int_rd((r - G.r_lut0) * G.r_lut_inv);
   bin = min(max(bin, 0), G.r_lut_n - 1);
-  const int2 e = __ldg(G.r_lut + bin);
-  return min(e.x + (r >= __int_as_float(e.y) ? 1 : 0), G.n_r - 2);
+  float base, split, r0, inv0, inv1, q0, q1, q2;
+  ldg8(G.r_bins + bin, base, split, r0, inv0, inv1, q0, q1, q2);
+  const bool up = r >= split;
+  R = up ? split : r0;
+  inv = up ? inv1 : inv0;
+  return __float_as_int(base) + (up ? 1 : 0);
 }
 
-__device__ __forceinline__ Sample eval_field(const GridDev& G, float x, float y, float z, bool want_te) {
+__device__ __forceinline__ int radial_cell(const GridDev& G, float r) {
+  float R, inv;
+  return radial_lookup(G, r, R, inv);
+}
+
+// The field at (x, y, z): trilinear n_e (and T_e when kTe and want_te) and
+// the exact gradient of the n_e interpolant.
+template <bool kTe>
+__device__ __forceinline__ Sample eval_field_t(const GridDev& G, float x, float y, float z, bool want_te) {
   const float rho2 = fmaf(x, x, y * y);
   const float r2 = fmaf(z, z, rho2);
   const float inv_r = rsqrtf(r2);
   const float r = r2 * inv_r;
   if (!(r <= G.r_vac)) return vacuum_sample();  // beyond the outer band (and NaN positions)
-  const int i = radial_cell(G, r);
-  const float2 rc = __ldg(G.r_cell + i);
-  const float u = (r - rc.x) * rc.y;
+  float R, inv_dr;
+  const int i = radial_lookup(G, r, R, inv_dr);
+  const float u = (r - R) * inv_dr;
 
   const float inv_rho = (rho2 > 0.f) ? rsqrtf(rho2) : 0.f;
   const float rho = rho2 * inv_rho;
@@ -153,7 +196,11 @@ __device__ __forceinline__ Sample eval_field(const GridDev& G, float x, float y,
   const float pp = ph * G.p_inv;
   const int k = min(max(__float2int_rd(pp), 0), G.n_p - 1);
   const float w = pp - (float)k;
-  return sample_cell(G, i, j, k, u, v, w, tsel, rc.y, x, y, z, inv_r, rho, inv_rho, want_te);
+  return sample_cell_t<kTe>(G, i, j, k, u, v, w, tsel, inv_dr, x, y, z, inv_r, rho, inv_rho, want_te);
+}
+
+__device__ __forceinline__ Sample eval_field(const GridDev& G, float x, float y, float z, bool want_te) {
+  return eval_field_t<true>(G, x, y, z, want_te);
 }
 
 // atan(num / den) with relative accuracy for small angles: the Taylor series
@@ -228,8 +275,8 @@ __device__ __forceinline__ Sample eval_field_off(const GridDev& G, const BasePoi
   const float dtt = atan_ratio(fmaf(c.z, drho, -c.rho * oz), fmaf(z, c.z, rho * c.rho)) * G.t_inv;
   const float dpp = atan_ratio(fmaf(c.x, oy, -c.y * ox), fmaf(c.x, x, c.y * y)) * G.p_inv;
 
-  int i = radial_cell(G, r);
-  float2 rcell = __ldg(G.r_cell + i);
+  float2 rcell;
+  int i = radial_lookup(G, r, rcell.x, rcell.y);
   float u = ((c.r - rcell.x) + dr) * rcell.y;
   if (u < 0.f && i > 0) {
     --i;

@@ -1,0 +1,342 @@
+// The persistent one-thread-per-bundle ray kernel (step-wise magnification
+// with 0, 2, 4 or 8 neighbours; Sec. 2.1 Eqs. 4-12, Sec. 3.2).
+//
+// Each thread owns one ray bundle at a time: the central ray of a (pixel,
+// frequency) and its NB step-wise neighbours.  Per central step i it
+//   (a) advances the central ray one RK4 step from node i (Eq. 4), with the
+//       stage-1 sample giving n_e and T_e at node i;
+//   (b) settles the transfer of segment i-1 -> i (Eq. 2 with Eq. 12, front to
+//       back) and the TAU_STOP / STEP_LIMIT terminations;
+//   (c) completes step i: chord t^i, transverse basis and eps (Eqs. 5, 6, 8),
+//       the new node, and the clip tests against the inner and outer spheres;
+//   (d) retraces step i for every neighbour seeded at r^i +- eps e_j with the
+//       central k^i (Eq. 7) and accumulates ln M^{i+1} (Eqs. 9-11);
+//   (e) on a clipped last step, closes the path at the crossing point.
+// This is the order of the paper's per-step description; the lane-parallel
+// bundle kernel (rt_bundle.cuh) computes the same quantities with the
+// neighbours one step behind the central lane.
+//
+// Why one thread per bundle.  The per-step bookkeeping (basis, ln M,
+// absorption, transfer, termination, compensated updates) is scalar per
+// bundle; with the bundle spread over NB + 1 lanes it ran on one lane of
+// NB + 1 and took a third of the warp's issue slots.  Here every lane of a
+// warp does useful work in every instruction, and a neighbour needs only the
+// first three RK4 stages (its separation depends on its end position, which
+// does not involve the fourth stage), so a step costs 4 + 3 NB field
+// evaluations instead of 4 (NB + 1).
+//
+// Precision (kMixed) and the offset form of the separations are those of
+// rt_bundle.cuh: d_j = eps e_j + h^2/12 (G_{+j} - G_{-j}) for a +-e_j pair,
+// ln M = log1p(c1.e1 + c2.e2 + t.(c1 x c2)) with c_j = (d_j - eps e_j) / eps.
+#pragma once
+#include "rt_bundle.cuh"
+
+namespace rt {
+
+#ifndef RT_RAY_MIN_BLOCKS
+#define RT_RAY_MIN_BLOCKS 6
+#endif
+constexpr int kRayMinBlocks = RT_RAY_MIN_BLOCKS;  // __launch_bounds__ occupancy target (128-thread blocks)
+
+// The sum G = a1 + a2 + a3 of the first three RK4 stages from (p, k): a
+// neighbour's end position is p + h k + h^2/6 G (the fourth stage enters only
+// the wave vector).  The arithmetic is that of rk4_step's G.
+__device__ __forceinline__ Vec rk4_g3(const GridDev& G, float kf, float h, float px, float py, float pz, float kx,
+                                      float ky, float kz) {
+  const float hh = 0.5f * h;
+  // stages 1 and 2 are independent (stage 2 sits at p + h/2 k)
+  Sample s1 = eval_field_t<false>(G, px, py, pz, false);
+  Sample s2 = eval_field_t<false>(G, fmaf(hh, kx, px), fmaf(hh, ky, py), fmaf(hh, kz, pz), false);
+  const float a1x = kf * s1.gx, a1y = kf * s1.gy, a1z = kf * s1.gz;
+  const float a2x = kf * s2.gx, a2y = kf * s2.gy, a2z = kf * s2.gz;
+  Vec g{a1x, a1y, a1z};
+  g.x += a2x; g.y += a2y; g.z += a2z;
+  // stage 3 at p + h/2 (k + h/2 a1)
+  const float qx = fmaf(hh, a1x, kx), qy = fmaf(hh, a1y, ky), qz = fmaf(hh, a1z, kz);
+  const Sample s3 = eval_field_t<false>(G, fmaf(hh, qx, px), fmaf(hh, qy, py), fmaf(hh, qz, pz), false);
+  g.x += kf * s3.gx; g.y += kf * s3.gy; g.z += kf * s3.gz;
+  return g;
+}
+
+// One central RK4 step (see rk4_step) with the stage-1 sample including T_e;
+// stages 1 and 2, and then 3 and 4, are independent of each other.
+__device__ __forceinline__ Rk4Out rk4_central(const GridDev& G, float kf, float h, float px, float py, float pz,
+                                              float kx, float ky, float kz) {
+  Rk4Out o;
+  const float hh = 0.5f * h;
+  const Sample s1 = eval_field_t<true>(G, px, py, pz, true);
+  const Sample s2 = eval_field_t<false>(G, fmaf(hh, kx, px), fmaf(hh, ky, py), fmaf(hh, kz, pz), false);
+  o.ne1 = s1.ne;
+  o.te1 = s1.te;
+  const float a1x = kf * s1.gx, a1y = kf * s1.gy, a1z = kf * s1.gz;
+  const float a2x = kf * s2.gx, a2y = kf * s2.gy, a2z = kf * s2.gz;
+  o.Gx = a1x; o.Gy = a1y; o.Gz = a1z;
+  o.Ax = a1x; o.Ay = a1y; o.Az = a1z;
+  o.Gx += a2x; o.Gy += a2y; o.Gz += a2z;
+  o.Ax = fmaf(2.f, a2x, o.Ax); o.Ay = fmaf(2.f, a2y, o.Ay); o.Az = fmaf(2.f, a2z, o.Az);
+  // stage 3 at p + h/2 (k + h/2 a1), stage 4 at p + h (k + h/2 a2)
+  const float qx = fmaf(hh, a1x, kx), qy = fmaf(hh, a1y, ky), qz = fmaf(hh, a1z, kz);
+  const float q3x = fmaf(hh, a2x, kx), q3y = fmaf(hh, a2y, ky), q3z = fmaf(hh, a2z, kz);
+  const Sample s3 = eval_field_t<false>(G, fmaf(hh, qx, px), fmaf(hh, qy, py), fmaf(hh, qz, pz), false);
+  const Sample s4 = eval_field_t<false>(G, fmaf(h, q3x, px), fmaf(h, q3y, py), fmaf(h, q3z, pz), false);
+  const float a3x = kf * s3.gx, a3y = kf * s3.gy, a3z = kf * s3.gz;
+  o.Gx += a3x; o.Gy += a3y; o.Gz += a3z;
+  o.Ax = fmaf(2.f, a3x, o.Ax); o.Ay = fmaf(2.f, a3y, o.Ay); o.Az = fmaf(2.f, a3z, o.Az);
+  o.Ax = fmaf(kf, s4.gx, o.Ax); o.Ay = fmaf(kf, s4.gy, o.Ay); o.Az = fmaf(kf, s4.gz, o.Az);
+  return o;
+}
+
+// "+" seed offset of neighbour pair j from the node: eps e1, eps e2, and (8
+// neighbours) eps (e1 + e2)/sqrt2, eps (e2 - e1)/sqrt2; the "-" member of the
+// pair sits at minus that offset.  a = eps e1, b = eps e2.
+__device__ __forceinline__ Vec pair_offset(int j, const Vec& a, const Vec& b) {
+  const float s2 = 0.70710678118654752f;
+  if (j == 0) return a;
+  if (j == 1) return b;
+  if (j == 2) return {s2 * (a.x + b.x), s2 * (a.y + b.y), s2 * (a.z + b.z)};
+  return {s2 * (b.x - a.x), s2 * (b.y - a.y), s2 * (b.z - a.z)};
+}
+
+template <int NB, bool kMixed>
+__global__ void __launch_bounds__(kThreads, kRayMinBlocks) trace_rays(const __grid_constant__ TraceParams P) {
+  const int lane = threadIdx.x & 31;
+  const float h = P.h;
+
+  // per-ray state; what is touched only when a ray starts or ends lives in
+  // shared memory (it would otherwise hold registers through every step)
+  struct Cold {
+    float* out;
+    RayDiag* dg;
+    unsigned long long steps_done, rays_done;
+    unsigned int item;
+  };
+  __shared__ Cold cold[kThreads];
+  Cold& C = cold[threadIdx.x];
+  C.out = nullptr;
+  C.dg = nullptr;
+  C.steps_done = 0;
+  C.rays_done = 0;
+  C.item = 0;
+  int step = 0;
+  bool active = false, exhausted = false;
+  float px = 0.f, py = 0.f, pz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
+  float rlx = 0.f, rly = 0.f, rlz = 0.f, klx = 0.f, kly = 0.f, klz = 0.f;  // compensation (kMixed)
+  float kf = 0.f, kap_c = 0.f, ln_f = 0.f;
+  float tau_hi = 0.f, tau_lo = 0.f, lns_hi = 0.f, lns_lo = 0.f, tb_hi = 0.f, tb_lo = 0.f;
+  float kap_prev = 0.f, te_prev = 0.f;
+
+  auto finish = [&](int st, float ex, float ey, float ez) {
+    *C.out = tb_hi + tb_lo;
+    RayDiag* dg = C.dg;
+    if (dg) {
+      RayDiag d;
+      d.exit_pos[0] = ex; d.exit_pos[1] = ey; d.exit_pos[2] = ez;
+      d.tau = tau_hi + tau_lo;
+      d.ln_s = lns_hi + lns_lo;
+      d.steps = step;
+      d.status = st;
+      *dg = d;
+    }
+    C.steps_done += (unsigned long long)step;
+    C.rays_done += 1;
+    active = false;
+  };
+
+  // one central step of this thread's bundle
+  auto step_once = [&]() {
+    // ---------------------------------------------- (a) central RK4 step
+    const Rk4Out o = rk4_central(P.G, kf, h, px, py, pz, kx, ky, kz);
+    const float kap = P.emission ? kappa_vac(o.ne1, o.te1, kap_c, ln_f) : 0.f;
+
+    // ---------------------------------------------- (b) segment step-1 -> step
+    if (step >= 1) {
+      const float dt = 0.5f * (kap_prev + kap) * P.hrsun;
+      const float tbar = 0.5f * (te_prev + o.te1);
+      const float tau0 = tau_hi + tau_lo;
+      acc_add<kMixed>(tb_hi, tb_lo, tbar * one_minus_exp_neg(dt) * __expf((lns_hi + lns_lo) - tau0));
+      acc_add<kMixed>(tau_hi, tau_lo, dt);
+      if (P.tau_stop > 0.f && tau_hi + tau_lo >= P.tau_stop) {
+        finish(kTauStop, px, py, pz);
+        return;
+      }
+      if (step >= P.max_steps) {
+        finish(kStepLimit, px, py, pz);
+        return;
+      }
+    }
+    if (P.ckpt && (step % kCkptEvery) == 0) {
+      // state at node `step` for the adjoint's recomputation (bounded by the ray's allocation)
+      const unsigned int item = C.item;
+      const unsigned long long slot = P.ck_off[item] + (unsigned long long)(step / kCkptEvery);
+      if (slot < P.ck_off[item + 1]) {
+        Ckpt& c = P.ckpt[slot];
+        c.r[0] = px; c.r[1] = py; c.r[2] = pz;
+        c.k[0] = kx; c.k[1] = ky; c.k[2] = kz;
+        c.rl[0] = rlx; c.rl[1] = rly; c.rl[2] = rlz;
+        c.kl[0] = klx; c.kl[1] = kly; c.kl[2] = klz;
+        c.tau_hi = tau_hi; c.tau_lo = tau_lo;
+        c.lns_hi = lns_hi; c.lns_lo = lns_lo;
+      }
+    }
+
+    // ---------------------------------------------- (c) complete step `step`
+    const Vec dr{fmaf(h, kx + klx, P.h2_6 * o.Gx), fmaf(h, ky + kly, P.h2_6 * o.Gy), fmaf(h, kz + klz, P.h2_6 * o.Gz)};
+    const Vec dk{P.h_6 * o.Ax, P.h_6 * o.Ay, P.h_6 * o.Az};
+    Vec rn, kn;
+    if (kMixed) {
+      fast_two_sum(px, dr.x + rlx, rn.x, rlx);
+      fast_two_sum(py, dr.y + rly, rn.y, rly);
+      fast_two_sum(pz, dr.z + rlz, rn.z, rlz);
+      fast_two_sum(kx, dk.x + klx, kn.x, klx);
+      fast_two_sum(ky, dk.y + kly, kn.y, kly);
+      fast_two_sum(kz, dk.z + klz, kn.z, klz);
+    } else {
+      rn = {px + dr.x, py + dr.y, pz + dr.z};
+      kn = {kx + dk.x, ky + dk.y, kz + dk.z};
+    }
+    kap_prev = kap;
+    te_prev = o.te1;
+    const float rr2 = dot3(rn, rn);
+    int term = 0;  // 0: carry on; else the status of a last step
+    if (rr2 < P.G.r_min * P.G.r_min) term = kHitInner;
+    else if (rr2 > P.G.r_max * P.G.r_max && dot3(rn, kn) > 0.f) term = kExitOuter;
+    else if (!isfinite(rr2 + kn.x + kn.y + kn.z)) term = kNan;
+
+    // ---------------------------------------------- (d) neighbour retrace of step `step`
+    if (NB > 0 && term != kNan) {
+      const float d2n = dot3(dr, dr);
+      const float ids = rsqrtf(d2n);
+      const Vec tp{dr.x * ids, dr.y * ids, dr.z * ids};  // chord direction (Eq. 5)
+      Vec e1, e2;
+      basis(tp, e1, e2);                                 // transverse basis (Eq. 6)
+      const float eps = (P.eps_fixed > 0.f) ? P.eps_fixed : P.eta * (d2n * ids);  // Eq. 8
+      const Vec sa{eps * e1.x, eps * e1.y, eps * e1.z}, sb{eps * e2.x, eps * e2.y, eps * e2.z};
+      // raw separations: NB >= 4: D_j = G_{+j} - G_{-j} over the +-pair j; NB == 2: G_j
+      constexpr int NP = (NB >= 4) ? NB / 2 : 2;
+      Vec D[NP];
+#pragma unroll 1
+      for (int j = 0; j < NP; ++j) {
+        Vec g;
+        if (NB >= 4) {
+          const Vec off = pair_offset(j, sa, sb);
+          const Vec gp = rk4_g3(P.G, kf, h, px + off.x, py + off.y, pz + off.z, kx, ky, kz);
+          const Vec gm = rk4_g3(P.G, kf, h, px - off.x, py - off.y, pz - off.z, kx, ky, kz);
+          g = {gp.x - gm.x, gp.y - gm.y, gp.z - gm.z};
+        } else {
+          const Vec off = (j == 0) ? sa : sb;
+          g = rk4_g3(P.G, kf, h, px + off.x, py + off.y, pz + off.z, kx, ky, kz);
+        }
+#pragma unroll
+        for (int m = 0; m < NP; ++m)
+          if (m == j) D[m] = g;
+      }
+      Vec c1, c2;
+      if (NB == 2) {  // one-sided: d_j = eps e_j + h^2/6 (G_j - G_0)
+        const float sc = P.h2_6 / eps;
+        c1 = {sc * (D[0].x - o.Gx), sc * (D[0].y - o.Gy), sc * (D[0].z - o.Gz)};
+        c2 = {sc * (D[1].x - o.Gx), sc * (D[1].y - o.Gy), sc * (D[1].z - o.Gz)};
+      } else {        // central difference: d = eps e + h^2/12 (G_+ - G_-)
+        const float sc = P.h2_12 / eps;
+        c1 = {sc * D[0].x, sc * D[0].y, sc * D[0].z};
+        c2 = {sc * D[1].x, sc * D[1].y, sc * D[1].z};
+      }
+      float lm = ln_m(c1, c2, e1, e2, tp);
+      if (NB == 8) {
+        const float s2 = 0.70710678118654752f, sc = P.h2_12 / eps;
+        const Vec g1{s2 * (e1.x + e2.x), s2 * (e1.y + e2.y), s2 * (e1.z + e2.z)};
+        const Vec g2{s2 * (e2.x - e1.x), s2 * (e2.y - e1.y), s2 * (e2.z - e1.z)};
+        const Vec c3{sc * D[2 % NP].x, sc * D[2 % NP].y, sc * D[2 % NP].z};
+        const Vec c4{sc * D[3 % NP].x, sc * D[3 % NP].y, sc * D[3 % NP].z};
+        const float lm2 = ln_m(c3, c4, g1, g2, tp);
+        // M = (M_e + M_g) / 2
+        lm = fmaxf(lm, lm2) + log1p_small(__expf(-fabsf(lm - lm2))) - 0.69314718055994531f;
+      }
+      acc_add<kMixed>(lns_hi, lns_lo, lm);
+    }
+
+    // ---------------------------------------------- (e) next node, or the end of the path
+    if (term == 0) {
+      px = rn.x; py = rn.y; pz = rn.z;
+      kx = kn.x; ky = kn.y; kz = kn.z;
+      step += 1;
+    } else if (term == kNan) {
+      step += 1;
+      finish(kNan, rn.x, rn.y, rn.z);
+    } else {
+      // clipped last segment + boundary term (Eq. 2 front to back); the
+      // crossing point closes the path
+      const Vec here{px, py, pz};
+      const float a = chord_crossing(here, dr, (term == kHitInner) ? P.G.r_min : P.G.r_max, term == kExitOuter);
+      const float cx = fmaf(a, dr.x, px), cy = fmaf(a, dr.y, py), cz = fmaf(a, dr.z, pz);
+      const Sample s = eval_field_t<true>(P.G, cx, cy, cz, true);
+      const float kap_e = P.emission ? kappa_vac(s.ne, s.te, kap_c, ln_f) : 0.f;
+      const float dt = 0.5f * (kap_prev + kap_e) * P.hrsun * a;
+      const float tbar = 0.5f * (te_prev + s.te);
+      const float lns = lns_hi + lns_lo;
+      acc_add<kMixed>(tb_hi, tb_lo, tbar * one_minus_exp_neg(dt) * __expf(lns - (tau_hi + tau_lo)));
+      acc_add<kMixed>(tau_hi, tau_lo, dt);
+      float tbc = 0.f;
+      if (term == kHitInner) tbc = (P.tbc_mode == 1) ? P.tbc_K : s.te;
+      if (tbc != 0.f) acc_add<kMixed>(tb_hi, tb_lo, tbc * __expf(lns - (tau_hi + tau_lo)));
+      step += 1;
+      finish(term, cx, cy, cz);
+    }
+  };
+
+  while (true) {
+    // ------------------------------------------------------------ refill
+    bool need = !active && !exhausted;
+    unsigned needmask = __ballot_sync(kFull, need);
+    while (needmask) {
+      const int leader = __ffs(needmask) - 1;
+      unsigned int first = 0;
+      if (lane == leader) first = atomicAdd(P.counter, (unsigned)__popc(needmask));
+      first = __shfl_sync(kFull, first, leader);
+      if (need) {
+        const unsigned int item = first + __popc(needmask & ((1u << lane) - 1u));
+        if (item >= P.total) {
+          exhausted = true;
+          need = false;
+        } else {
+          const RayStart rs = start_ray(P, item);
+          C.item = item;
+          C.out = rs.out;
+          C.dg = rs.dg;
+          if (rs.valid) {  // a ragged chunk tail has no ray behind the ticket: take another
+            kf = P.straight ? 0.f : rs.F->kf;
+            kap_c = rs.F->kap_c;
+            ln_f = rs.F->ln_f;
+            step = 0;
+            tau_hi = tau_lo = lns_hi = lns_lo = tb_hi = tb_lo = 0.f;
+            rlx = rly = rlz = klx = kly = klz = 0.f;
+            kap_prev = te_prev = 0.f;
+            if (!rs.enter) {
+              finish(kMiss, rs.px, rs.py, rs.pz);
+            } else {
+              px = rs.px; py = rs.py; pz = rs.pz;
+              kx = rs.kx; ky = rs.ky; kz = rs.kz;
+              active = true;
+              need = false;
+            }
+          }
+        }
+      }
+      needmask = __ballot_sync(kFull, need);
+    }
+    if (!__any_sync(kFull, active)) break;
+    if (active) step_once();
+  }
+
+  // ---- statistics
+  unsigned long long steps_done = C.steps_done, rays_done = C.rays_done;
+  for (int off = 16; off > 0; off >>= 1) {
+    steps_done += __shfl_down_sync(kFull, steps_done, off);
+    rays_done += __shfl_down_sync(kFull, rays_done, off);
+  }
+  if (lane == 0 && P.stats) {
+    atomicAdd(P.stats, steps_done);
+    atomicAdd(P.stats + 1, rays_done);
+  }
+}
+
+}  // namespace rt

@@ -122,3 +122,104 @@ def test_backward_reuses_forward_diag(rt, ctx):
     assert not torch.equal(d_other[..., 5], d[..., 5])
     with pytest.raises(RuntimeError, match="fwd_diag"):
         ctx.backward(grid, v, [60e6], w, opts, fwd_diag=d_other)
+
+
+@pytest.fixture(scope="module")
+def misfit_case(orc):
+    """The differentiation workload (128x90x180 corona, 256x256 x 8 frequencies
+    40-400 MHz, step 2e-3 R_sun, 4 step-wise neighbours): the misfit
+    L = sum (T_b - T_target)^2 over 32 seeded pixels of the image at all 8
+    frequencies (the oracle's cost bounds the sample), T_target traced by the
+    oracle through the perturbed copy of the grid (n_e x (1 + 0.1 N(0,1)),
+    smoothed over one cell).  Holds the oracle's side: its T_b, its tape
+    gradient for dL/dT_b = 2 (T_b - T_target), and central differences of L
+    on 64 n_e and 32 T_e nodes drawn among those with a gradient above 1e-3
+    of the largest.
+
+    Step of the differences: a relative 1e-6 of the node value.  The
+    trilinear interpolant's gradient jumps at cell faces, so L is smooth only
+    between the values at which some RK4 stage point crosses a face; the
+    step must be small enough that rarely happens (at 1e-4, 7 of 12 nodes
+    straddled one) and large enough to stay above the FP64 rounding of
+    ~3000-step paths (at 1e-8 the differences scatter by 1e-2)."""
+    g, v, f = cs.adjoint_workload()
+    gt = cs.perturbed_target(g)
+    rng = np.random.default_rng(41)
+    pix = np.sort(rng.choice(v.nx * v.ny, size=32, replace=False)).astype(np.int32)
+    opts = orc.default_options(tau_stop=30.0)
+    tgt = orc.trace(orc.grid_field(gt), v, f, opts, pixels=pix)["tb"]
+    ne64, te64 = g.ne.astype(np.float64), g.te.astype(np.float64)
+
+    def loss(ne, te):
+        r = orc.trace(orc.grid_field(cs.Grid(g.r, g.theta, g.phi, ne, te)), v, f, opts, pixels=pix)
+        return float(((r["tb"] - tgt) ** 2).sum()), r
+
+    L0, r0 = loss(ne64, te64)
+    w = 2.0 * (r0["tb"] - tgt)
+    gne, gte, _ = orc.backward(orc.grid_field(g), v, f, w, opts, pixels=pix)
+    fd = {}
+    for which, n, tape, base in (("ne", 64, gne, ne64), ("te", 32, gte, te64)):
+        cells = cs.fd_cells(tape.shape, n=n, mask=np.abs(tape) > 1e-3 * np.abs(tape).max())
+        vals = []
+        for c in cells:
+            d = 1e-6 * base.flat[c]
+            side = []
+            for sgn in (1.0, -1.0):
+                a = base.copy()
+                a.flat[c] += sgn * d
+                L, r = loss(a, te64) if which == "ne" else loss(ne64, a)
+                event = bool((r["steps"] != r0["steps"]).any() or (r["status"] != r0["status"]).any())
+                side.append((L, event))
+            vals.append(((side[0][0] - side[1][0]) / (2 * d), side[0][1] or side[1][1]))
+        fd[which] = (cells, vals)
+    return dict(g=g, v=v, f=f, pix=pix, tgt=tgt, w=w, gne=gne, gte=gte, fd=fd)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_differentiation_workload_against_tape_and_fd(rt, ctx, misfit_case, precision):
+    """rt_backward on the differentiation workload's misfit (Sec. 2.1 Eqs. 4-12
+    differentiated; the workload's step 2e-3 R_sun) against
+      (a) the oracle's FP64 tape adjoint with the same dL/dT_b, at every node
+          (relative L2 <= 5e-3; <= 2e-2 on nodes above 1% of the largest), and
+      (b) the FP64 central differences of the oracle's misfit (misfit_case),
+          <= 1e-2 per node.  A node whose +-step changes a ray's step count or
+          status, or where the tape adjoint (which holds the discrete events
+          fixed) and the differences disagree by more than 2e-3, straddles a
+          discrete event and is excluded with a count; at least 3/4 of the
+          nodes must remain.
+    The GPU side's own dL/dT_b = 2 (T_b - T_target), from its own maps, is
+    checked against the differences (b) too."""
+    import torch
+    M = misfit_case
+    g, v, f, pix, tgt = M["g"], M["v"], M["f"], M["pix"], M["tgt"]
+    grid = ctx.load(g)
+    o = rt.options(precision=precision)
+    tb_gpu = ctx.trace_image(grid, v, f, o).cpu().numpy().reshape(len(f), -1)[:, pix].astype(np.float64)
+    wmap = np.zeros((len(f), v.ny * v.nx))
+    wmap[:, pix] = M["w"]
+    dne, dte = ctx.backward(grid, v, f, wmap.reshape(len(f), v.ny, v.nx), o)
+    wmap[:, pix] = 2.0 * (tb_gpu - tgt)
+    dne_own, dte_own = ctx.backward(grid, v, f, wmap.reshape(len(f), v.ny, v.nx), o)
+    torch.cuda.synchronize()
+    report = {"precision": precision,
+              "tape_rel_l2_ne": compare_grads(dne, M["gne"], f"dne (tape) precision {precision}"),
+              "tape_rel_l2_te": compare_grads(dte, M["gte"], f"dte (tape) precision {precision}")}
+    for which, tape, gpu, own in (("ne", M["gne"], dne, dne_own), ("te", M["gte"], dte, dte_own)):
+        cells, vals = M["fd"][which]
+        gg = gpu.cpu().numpy().astype(np.float64).ravel()
+        go = own.cpu().numpy().astype(np.float64).ravel()
+        errs, errs_own, excluded = [], [], 0
+        for c, (d_fd, event) in zip(cells, vals):
+            if event or abs(tape.flat[c] - d_fd) > 2e-3 * abs(d_fd):
+                excluded += 1
+                continue
+            errs.append(abs(gg[c] - d_fd) / abs(d_fd))
+            errs_own.append(abs(go[c] - d_fd) / abs(d_fd))
+        report[which] = {"cells": len(cells), "excluded": excluded, "max_rel_err": max(errs),
+                         "max_rel_err_own_weights": max(errs_own)}
+    print("differentiation workload", report)
+    for which in ("ne", "te"):
+        r = report[which]
+        assert r["cells"] - r["excluded"] >= 0.75 * r["cells"], (which, r)
+        assert r["max_rel_err"] <= 1e-2, (which, r)
+        assert r["max_rel_err_own_weights"] <= 1e-2, (which, r)

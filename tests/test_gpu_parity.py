@@ -1,26 +1,29 @@
 """GPU parity: librt's CUDA path against the FP64 oracle, element by element
 on the same seeded inputs, through the C ABI.
 
-Bars.
-  strict (well-conditioned rays; the spherically symmetric corona):
-    |dT_b| <= 1e-3 * max(T_b, 1e-2 * max over the map of T_b),
-    exit position <= 1e-4 R_sun for rays ending on a sphere, same status.
-  conditioned (non-symmetric coronae): a ray's path on the trilinear
-    interpolant is chaotic where stage points fall within rounding distance
-    of a cell face (the interpolant's gradient jumps there).  The oracle
-    measures each ray's own single-precision conditioning by re-tracing it
-    with r, theta, phi perturbed at the 1e-6 level (six seeds; the GPU's
-    single-precision geometry errs by ~3e-7: a face flip is a rare event per
-    stage point, so a single seed finds one only now and then); a ray must
-    match within max(strict bar, 10 x its spread) in T_b, exit and ln S,
-    with the same status
-    unless the status itself flips under the perturbation, and at least 60%
-    of the rays must be well-conditioned in T_b (spread below a tenth of the
-    T_b bar) so that the bounds are not vacuous (30% in tube mode, whose
-    persistent neighbours are intrinsically worse conditioned: TUBE_MIN_WELL).
-  ln S (compensated form): 1e-3 absolute.  Near a turning point n -> 0, so
-    eps = eta |dr| -> 0 (Eq. 8) and FP32 neighbour geometry resolves the
-    pair separation only to ulp(r) / eps.
+Bars (the strict bars are the tolerances of the method's FP32 form):
+  T_b:   |dT_b| <= 1e-3 * max(T_b, 1e-2 * max over the map of T_b);
+  exit:  the exit position of a ray ending on a sphere within 1e-4 R_sun;
+  status equal; ln(S_N / S_0) within lns_abs where a test states it.
+
+Conditioning.  A ray's path on the trilinear interpolant is chaotic where
+stage points fall within rounding distance of a cell face (the
+interpolant's gradient jumps there), so on a corona that is rough at the
+cell scale no FP32 implementation reproduces every FP64 ray.  The oracle
+measures each ray's own sensitivity by re-tracing it with every lookup's r
+perturbed by a relative 1e-7 and theta, phi by 3e-7 rad (the size of the
+GPU's FP32 geometry rounding; eight seeds, since a face flip is a rare event
+per stage point).  A ray is well-conditioned when no seed flips its status
+and the largest change stays below a tenth of each bar (T_b, and the exit
+and ln S where they are checked).  Every well-conditioned ray is held to the
+strict bars.  An ill-conditioned ray is held to max(strict bar, 10 x its
+spread) in T_b, capped at 1e-2 of the scale (TB_CAP), and its status only if
+the status did not flip under the probe; its exit point and ln S are
+reported, not bounded (on chaotic rays they differ by up to whole R_sun
+between two correct FP32 runs).  Each test states the fraction of its rays
+that must be well-conditioned (the bound is not vacuous) and prints, per
+frequency, the fraction that is, the largest T_b bound granted and the
+largest exit difference among the ill-conditioned rays.
 """
 import numpy as np
 import pytest
@@ -31,7 +34,9 @@ pytestmark = pytest.mark.gpu
 
 TB_REL = 1e-3
 EXIT_ABS = 1e-4
-JITTER = 1e-6
+TB_CAP = 1e-2
+JITTER = 1e-7
+SEEDS = 8
 
 
 @pytest.fixture(scope="module")
@@ -87,7 +92,7 @@ def spreads(orc, g, v, freqs, ref, pixels=None, **opt):
     sex = np.zeros(ref["tb"].shape)
     sls = np.zeros(ref["tb"].shape)
     flip = np.zeros(ref["tb"].shape, bool)
-    for seed in range(1, 7):
+    for seed in range(1, SEEDS + 1):
         j = run_oracle(orc, g, v, freqs, pixels=pixels, jitter=JITTER, jitter_seed=seed, **dict(opt))
         stb = np.maximum(stb, np.abs(j["tb"] - ref["tb"]))
         sex = np.maximum(sex, np.linalg.norm(j["exit"] - ref["exit"], axis=-1))
@@ -101,50 +106,67 @@ def _scale(ref_tb):
 
 
 def compare(gpu, ref, pixels=None, tb_rel=TB_REL, exit_abs=EXIT_ABS, lns_abs=None, cond=None, label="",
-            min_well=0.6):
+            min_well=0.6, freqs=None):
+    """Element-by-element comparison (see the module docstring for the bars);
+    returns a report with the per-frequency fraction of well-conditioned rays."""
     sel = (lambda a: a) if pixels is None else (lambda a: a[:, pixels])
     g_tb, g_st, g_ex, g_ls = sel(gpu["tb"]), sel(gpu["status"]), sel(gpu["exit"]), sel(gpu["ln_s"])
     scale = _scale(ref["tb"])
     dtb = np.abs(g_tb - ref["tb"])
     dex = np.linalg.norm(g_ex - ref["exit"], axis=-1)
+    dls = np.abs(g_ls - ref["ln_s"])
     ends = (ref["status"] == 1) | (ref["status"] == 2)
     if cond is None:
         well = np.ones(ref["tb"].shape, bool)
+        flip = np.zeros(ref["tb"].shape, bool)
         tb_bound = tb_rel * scale
-        ex_bound = np.full(dex.shape, exit_abs)
     else:
         stb, sex, sls, flip = cond
-        well = ~flip
-        tb_bound = np.maximum(tb_rel * scale, 10 * stb)
-        ex_bound = np.maximum(exit_abs, 10 * sex)
-    bad_st = well & (g_st != ref["status"])
+        well = ~flip & (stb <= 0.1 * tb_rel * scale) & (~ends | (sex <= 0.1 * exit_abs))
+        if lns_abs is not None:
+            well &= sls <= 0.1 * max(lns_abs, 1e-30)
+        tb_bound = np.where(well, tb_rel * scale,
+                            np.minimum(np.maximum(tb_rel * scale, 10 * stb), TB_CAP * scale))
+    bad_st = ~flip & (g_st != ref["status"])
     assert not bad_st.any(), f"{label}: status differs at {np.argwhere(bad_st)[:5]}"
     bad_tb = dtb > tb_bound
     if bad_tb.any():
         idx = [tuple(i) for i in np.argwhere(bad_tb)[:4]]
-        det = [(i, g_tb[i], ref["tb"][i], tb_bound[i], cond[0][i] if cond else None) for i in idx]
-        raise AssertionError(f"{label}: T_b out of bounds (idx, gpu, oracle, bound, spread) {det}; "
+        det = [(i, g_tb[i], ref["tb"][i], tb_bound[i], bool(well[i]), cond[0][i] if cond else None) for i in idx]
+        raise AssertionError(f"{label}: T_b out of bounds (idx, gpu, oracle, bound, well, spread) {det}; "
                              f"max rel {(dtb / scale).max():.3e}")
-    chk = ends & well & (g_st == ref["status"])
-    if chk.any():
-        bad_ex = chk & (dex > ex_bound)
-        if bad_ex.any():
-            idx = [tuple(i) for i in np.argwhere(bad_ex)[:4]]
-            det = [(i, dex[i], ex_bound[i], cond[1][i] if cond else None, ref["status"][i]) for i in idx]
-            raise AssertionError(f"{label}: exit error (idx, err, bound, spread, status) {det}")
+    chk = ends & well
+    bad_ex = chk & (dex > exit_abs)
+    if bad_ex.any():
+        idx = [tuple(i) for i in np.argwhere(bad_ex)[:4]]
+        det = [(i, dex[i], cond[1][i] if cond else None, ref["status"][i]) for i in idx]
+        raise AssertionError(f"{label}: exit error of well-conditioned rays (idx, err, spread, status) {det}")
     if lns_abs is not None:
-        ls_bound = np.full(dex.shape, lns_abs) if cond is None else np.maximum(lns_abs, 10 * cond[2])
-        bad_ls = well & (np.abs(g_ls - ref["ln_s"]) > ls_bound)
+        bad_ls = well & (dls > lns_abs)
         if bad_ls.any():
             idx = [tuple(i) for i in np.argwhere(bad_ls)[:4]]
-            det = [(i, g_ls[i], ref["ln_s"][i], ls_bound[i]) for i in idx]
-            raise AssertionError(f"{label}: ln S out of bounds (idx, gpu, oracle, bound) {det}")
-    if cond is not None:
-        # the per-ray bounds must not be vacuous: most rays are well-conditioned
-        frac = (cond[0] <= 0.1 * tb_rel * scale).mean()
-        assert frac >= min_well, f"{label}: only {frac:.0%} of rays well-conditioned in T_b"
-    return {"max_tb_rel": float((dtb / scale).max()), "max_exit": float(dex[ends].max()) if ends.any() else 0.0,
-            "no_flip": float(well.mean())}
+            det = [(i, g_ls[i], ref["ln_s"][i]) for i in idx]
+            raise AssertionError(f"{label}: ln S of well-conditioned rays out of bounds (idx, gpu, oracle) {det}")
+    frac = float(well.mean())
+    per_f = []
+    for fi in range(ref["tb"].shape[0]):
+        ill = ~well[fi]
+        per_f.append({"f_MHz": None if freqs is None else round(float(freqs[fi]) / 1e6, 2),
+                      "well": round(float(well[fi].mean()), 4),
+                      "max_tb_rel_well": float((dtb[fi] / scale[fi])[well[fi]].max()) if well[fi].any() else 0.0,
+                      "max_tb_bound_rel": float((tb_bound[fi] / scale[fi]).max()),
+                      "max_exit_well": float(dex[fi][well[fi] & ends[fi]].max()) if (well[fi] & ends[fi]).any()
+                      else 0.0,
+                      "max_exit_ill": float(dex[fi][ill & ends[fi]].max()) if (ill & ends[fi]).any() else 0.0})
+    report = {"label": label, "rays": int(well.size), "well": round(frac, 4),
+              "max_tb_rel": float((dtb / scale).max()),
+              "max_tb_rel_well": float((dtb / scale)[well].max()) if well.any() else 0.0,
+              "max_exit_well": float(dex[chk].max()) if chk.any() else 0.0,
+              "max_lns_well": float(dls[well].max()) if well.any() else 0.0,
+              "per_frequency": per_f}
+    print("parity", report)
+    assert frac >= min_well, f"{label}: only {frac:.1%} of rays well-conditioned (need {min_well:.0%})"
+    return report
 
 
 # ------------------------------------------------------------ field row
@@ -377,15 +399,21 @@ def sample_pixels(nx, ny, n, seed=0):
 def test_global_corona_sampled(rt, ctx, orc):
     """The 256x180x360 MAS-like corona, 512x512 x 16 frequencies, in the
     launch configuration the benchmark times; 48 sampled pixels at every
-    frequency against the oracle, within each ray's conditioning."""
+    frequency against the oracle.  Well-conditioned rays (GLOBAL_MIN_WELL of
+    them at least) meet the strict T_b, exit and ln S bars; the others the
+    capped conditioned T_b bound."""
     g, v, f = cs.global_workload()
     grid = ctx.load(g)
     gpu = run_gpu(rt, ctx, grid, v, f, precision=1)
     pix = sample_pixels(v.nx, v.ny, 48, seed=1)
     ref = run_oracle(orc, g, v, f, pixels=pix)
     cond = spreads(orc, g, v, f, ref, pixels=pix)
-    res = compare(gpu, ref, pixels=pix, cond=cond, label="global mixed")
-    print("global parity", res)
+    compare(gpu, ref, pixels=pix, cond=cond, lns_abs=GLOBAL_LNS_ABS, label="global mixed", freqs=f,
+            min_well=GLOBAL_MIN_WELL)
     # invariants at full size: every ray finished with a terminal status
     assert np.isin(gpu["status"], [1, 2, 3, 5]).all()
     assert np.isfinite(gpu["tb"]).all() and (gpu["tb"] >= 0).all()
+
+
+GLOBAL_LNS_ABS = 1e-3
+GLOBAL_MIN_WELL = 0.6

@@ -639,3 +639,17 @@ def test_stepwise_eps_at_slab_surface(orc):
         eps = eta * np.linalg.norm(dr)
         m = orc.stepwise_m(F, f, orc.default_options(dtau=h, eta=eta, n_nb=4), r0, k0)
         assert (m - 1) == pytest.approx(-h * h * A / (4 * eps), rel=2e-3)
+
+
+def test_disk_mean_closed_forms(orc):
+    """The disk-mean spectrum (Sec. 3.4): a constant map averages to the
+    constant; the map u^2 + v^2 averages to radius^2 / 2 over a finely
+    sampled disk (the mean of rho^2 over a disk of radius R); a radius that
+    holds no pixel centre gives 0."""
+    v = cs.View(0.0, 0.0, 400, 400, -1.0, 1.0, -1.0, 1.0)
+    assert np.allclose(orc.disk_mean_tb(v, np.full((2, 400, 400), 3.5e5)), 3.5e5, rtol=1e-14)
+    u = -1.0 + (np.arange(400) + 0.5) * (2.0 / 400)
+    rho2 = u[None, :] ** 2 + u[:, None] ** 2
+    assert orc.disk_mean_tb(v, rho2[None], 0.5)[0] == pytest.approx(0.125, rel=2e-3)
+    assert orc.disk_mean_tb(v, rho2[None], 1e-4)[0] == 0.0
+
