@@ -233,10 +233,14 @@ rt_status rt_trace_batch(rt_ctx* ctx, const rt_grid* grid, const rt_request* req
  * scattering node gradients with atomics.
  * view, freqs_hz, nf, opt: as for rt_trace_image; supported forms: s_mode
  * RT_STEPWISE with n_nb = 4, or RT_MAG_OFF; not straight lines of sight.
- * dL_dTb:  device [nf][ny][nx] float.
+ * dL_dTb:  device [nf][ny][nx] float.  A ray whose weight is exactly 0 cannot
+ *          contribute and is not traced by any pass of the call (so a
+ *          caller that splits the rays between GPUs by zeroing the others'
+ *          weights does only its own share of the work).
  * dL_dne, dL_dte: device [n_r][n_theta][n_phi] float, caller-owned,
  *          overwritten (zeroed by the call first).
- * tb_out:  device [nf][ny][nx] float for the forward T_b, or NULL.
+ * tb_out:  device [nf][ny][nx] float for the forward T_b (0 for rays with a
+ *          zero weight), or NULL.
  * fwd_diag: optional device [nf][ny][nx] rt_ray_diag that rt_trace_image
  *          returned for the same grid, view, frequencies and options (an
  *          autograd forward keeps it).  The checkpoints are sized from its

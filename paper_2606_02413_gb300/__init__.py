@@ -68,11 +68,22 @@ class Grid:
             pass
 
 
+class ImageRequest:
+    """One image request of a batch: a view and its frequencies [Hz]."""
+
+    def __init__(self, view, freqs_hz):
+        self.view = view
+        self.freqs_hz = freqs_hz
+
+
 class BatchPlan:
     """rt_batch_plan: one graph-captured persistent launch over many requests.
-    ``outputs`` holds each request's T_b tensor [nf, ny, nx] (and diag)."""
+    ``outputs`` holds each request's T_b tensor [nf, ny, nx] (and diag).
+    shard=(rank, world_size): the plan of one rank of a multi-GPU partition
+    (rt_batch_plan_create_shard); its outputs start at zero and hold only
+    that rank's rays."""
 
-    def __init__(self, ctx: "Context", grid: Grid, requests, opts=None, diag=False):
+    def __init__(self, ctx: "Context", grid: Grid, requests, opts=None, diag=False, shard=None):
         import torch
         self.ctx = ctx
         self._keep = []
@@ -83,8 +94,9 @@ class BatchPlan:
         for i, req in enumerate(requests):
             v = view(req.view)
             f = np.ascontiguousarray(np.atleast_1d(req.freqs_hz), dtype=np.float64)
-            tb = torch.empty((len(f), v.ny, v.nx), dtype=torch.float32, device=dev)
-            d = torch.empty((len(f), v.ny, v.nx, 7), dtype=torch.int32, device=dev) if diag else None
+            alloc = torch.zeros if shard is not None else torch.empty
+            tb = alloc((len(f), v.ny, v.nx), dtype=torch.float32, device=dev)
+            d = alloc((len(f), v.ny, v.nx, 7), dtype=torch.int32, device=dev) if diag else None
             self._keep += [v, f]
             arr[i] = _abi.Request(C.pointer(v), f.ctypes.data_as(C.POINTER(C.c_double)), len(f), tb.data_ptr(),
                                   d.data_ptr() if d is not None else None)
@@ -92,8 +104,12 @@ class BatchPlan:
         self._arr = arr
         o = opts if opts is not None else options()
         h = C.c_void_p()
-        check(lib().rt_batch_plan_create(ctx.handle, grid.handle, arr, n, C.byref(o), C.byref(h)),
-              "rt_batch_plan_create")
+        if shard is None:
+            check(lib().rt_batch_plan_create(ctx.handle, grid.handle, arr, n, C.byref(o), C.byref(h)),
+                  "rt_batch_plan_create")
+        else:
+            check(lib().rt_batch_plan_create_shard(ctx.handle, grid.handle, arr, n, C.byref(o), int(shard[0]),
+                                                   int(shard[1]), C.byref(h)), "rt_batch_plan_create_shard")
         self.handle = h
 
     def launch(self, stream=None):

@@ -65,6 +65,30 @@ def _time(ctx, grid, v, freqs, opts, reps=2):
     return best
 
 
+def step_gate(ctx, grid, v, freqs, opts=None, gate=1e-3, side=32):
+    """The step-size part of tune(): the largest step in STEPS whose side^2
+    maps of the field of view of v stay within `gate` (every pixel) of the
+    maps at the smallest step.  Returns (dtau, {step: worst error},
+    {step: 99th-percentile error})."""
+    from types import SimpleNamespace
+    opts = opts if opts is not None else make_options()
+    vs = make_view(v)
+    freqs = np.atleast_1d(np.asarray(freqs, dtype=np.float64))
+    base = _fields(opts)
+    small = SimpleNamespace(lon_rad=vs.lon_rad, lat_rad=vs.lat_rad, nx=side, ny=side, x0=vs.x0, x1=vs.x1,
+                            y0=vs.y0, y1=vs.y1)
+    ref = ctx.trace_image(grid, small, freqs, make_options(**{**base, "dtau": STEPS[0]}))
+    dtau, worst, p99 = STEPS[0], {}, {}
+    for h in STEPS:
+        tb = ctx.trace_image(grid, small, freqs, make_options(**{**base, "dtau": h}))
+        rel = _rel_err(tb, ref)
+        worst[f"{h:g}"] = float(rel.max())                    # the gate: every pixel
+        p99[f"{h:g}"] = float(np.percentile(rel, 99))         # reported only
+        if worst[f"{h:g}"] <= gate:
+            dtau = h
+    return dtau, worst, p99
+
+
 def tune(ctx, grid, v, freqs, opts=None, gate=1e-3, cache=None, time_side=128, tune_step=True):
     """Returns (rt_options with dtau, tile and blocks_per_sm set, report)."""
     from types import SimpleNamespace
@@ -83,18 +107,7 @@ def tune(ctx, grid, v, freqs, opts=None, gate=1e-3, cache=None, time_side=128, t
     # 1) step size on a 32x32 image of the same field of view
     dtau = base["dtau"]
     if tune_step:
-        small = SimpleNamespace(lon_rad=vs.lon_rad, lat_rad=vs.lat_rad, nx=32, ny=32, x0=vs.x0, x1=vs.x1,
-                                y0=vs.y0, y1=vs.y1)
-        ref = ctx.trace_image(grid, small, freqs, make_options(**{**base, "dtau": STEPS[0]}))
-        dtau = STEPS[0]
-        for h in STEPS:
-            tb = ctx.trace_image(grid, small, freqs, make_options(**{**base, "dtau": h}))
-            rel = _rel_err(tb, ref)
-            err = float(rel.max())
-            report["steps"][f"{h:g}"] = err                                  # the gate: every pixel
-            report["steps_p99"][f"{h:g}"] = float(np.percentile(rel, 99))   # reported only
-            if err <= gate:
-                dtau = h
+        dtau, report["steps"], report["steps_p99"] = step_gate(ctx, grid, v, freqs, opts, gate)
     # 2) launch shape on a reduced image at the chosen step
     red = SimpleNamespace(lon_rad=vs.lon_rad, lat_rad=vs.lat_rad, nx=min(vs.nx, time_side),
                           ny=min(vs.ny, time_side), x0=vs.x0, x1=vs.x1, y0=vs.y0, y1=vs.y1)

@@ -15,7 +15,7 @@
 //               applied to lambda, obtained as the tangent of g evaluated on
 //               dual numbers x + lambda (cell held fixed).
 #pragma once
-#include "rt_bundle.cuh"
+#include "rt_rays.cuh"
 
 namespace rt {
 
@@ -132,8 +132,9 @@ __device__ __forceinline__ Vec value_adjoint(const GridDev& G, float x, float y,
 // kf H(p) lam (the position adjoint), H from dual numbers with the cell fixed.
 __device__ __forceinline__ Vec force_adjoint(const GridDev& G, float kf, float x, float y, float z, const Vec& lam,
                                              float* dne) {
+  if (lam.x == 0.f && lam.y == 0.f && lam.z == 0.f) return {0.f, 0.f, 0.f};
   const CellGeom c = cell_geom(G, x, y, z);
-  if (c.vac || (lam.x == 0.f && lam.y == 0.f && lam.z == 0.f)) return {0.f, 0.f, 0.f};
+  if (c.vac) return {0.f, 0.f, 0.f};
   // node scatter
   const float gu = lam.x * c.du.x + lam.y * c.du.y + lam.z * c.du.z;
   const float gv = lam.x * c.dv.x + lam.y * c.dv.y + lam.z * c.dv.z;
@@ -239,6 +240,27 @@ __device__ __forceinline__ void rk4_reverse(const GridDev& G, float kf, float h,
   lk_out = {lk_out.x + Lk.x, lk_out.y + Lk.y, lk_out.z + Lk.z};
 }
 
+// Reverse of a neighbour's retrace (rk4_g3): its separation uses only
+// G = a1 + a2 + a3, so given lg = dL/dG the adjoints flow through stages 3,
+// 2, 1 (stage 3 sits at p + h/2 (k + h/2 a1), stage 2 at p + h/2 k).  Adds
+// dL/dp and dL/dk of the seed to lp, lk and scatters the n_e nodes.
+__device__ __forceinline__ void rk4_g3_reverse(const GridDev& G, float kf, float h, const Vec& p, const Vec& k,
+                                               const Vec& lg, Vec& lp, Vec& lk, float* dne) {
+  const float hh = 0.5f * h;
+  const Sample s1 = eval_field_t<false>(G, p.x, p.y, p.z, false);
+  const Vec a1{kf * s1.gx, kf * s1.gy, kf * s1.gz};
+  const Vec k2{fmaf(hh, a1.x, k.x), fmaf(hh, a1.y, k.y), fmaf(hh, a1.z, k.z)};
+  // stage 3
+  const Vec Lp3 = force_adjoint(G, kf, fmaf(hh, k2.x, p.x), fmaf(hh, k2.y, p.y), fmaf(hh, k2.z, p.z), lg, dne);
+  // stage 2
+  const Vec Lp2 = force_adjoint(G, kf, fmaf(hh, k.x, p.x), fmaf(hh, k.y, p.y), fmaf(hh, k.z, p.z), lg, dne);
+  // stage 1 (a1 enters G and, through k2, the stage-3 point)
+  const Vec La1{fmaf(hh * hh, Lp3.x, lg.x), fmaf(hh * hh, Lp3.y, lg.y), fmaf(hh * hh, Lp3.z, lg.z)};
+  const Vec Lp1 = force_adjoint(G, kf, p.x, p.y, p.z, La1, dne);
+  lp = {lp.x + Lp1.x + Lp2.x + Lp3.x, lp.y + Lp1.y + Lp2.y + Lp3.y, lp.z + Lp1.z + Lp2.z + Lp3.z};
+  lk = {fmaf(hh, Lp2.x + Lp3.x, lk.x), fmaf(hh, Lp2.y + Lp3.y, lk.y), fmaf(hh, Lp2.z + Lp3.z, lk.z)};
+}
+
 // d kappa_vac / d n_e and d kappa_vac / d T_e (see kappa_vac).
 __device__ __forceinline__ void kappa_partials(float ne, float te, float kap_c, float ln_f, float& dk_dne,
                                                float& dk_dte) {
@@ -254,17 +276,6 @@ __device__ __forceinline__ void kappa_partials(float ne, float te, float kap_c, 
 }
 
 // ------------------------------------------------------------ the kernel
-// Per-step record of one recomputed segment (node m = m0 + j).
-struct StepRec {
-  float r[3], k[3], dr[3];     // node state and the chord increment of step m
-  float kap, te, ne, tau;      // node transfer values; tau before segment m
-  float lns_next, lnm;         // ln S at node m+1 and ln M^{m+1}
-  float c1[3], c2[3];          // scaled tube separations of step m
-  float t[3], e1[3], e2[3];    // chord direction and transverse basis of step m
-  float eps;
-  int axis;                    // basis reference: 0 z, 1 y
-};
-
 struct AdjParams {
   GridDev G;
   float h, h2_6, h_6, h2_12, hrsun, eta, eps_fixed, tbc_K;
@@ -276,7 +287,6 @@ struct AdjParams {
   const float* dL_dTb;         // [nf][npix], output order
   const Ckpt* ckpt;
   const unsigned long long* ck_off;
-  StepRec* rec;                // [slots][kCkptEvery + 1]
   float* dne;
   float* dte;
   unsigned int* counter;
@@ -284,50 +294,49 @@ struct AdjParams {
   unsigned long long* mismatch;  // rays whose step count does not match their checkpoint allocation
 };
 
-struct AdjState {
-  int N, status, seg, clipped;
-  float kf, kn2, kap_c, ln_f, lamT, alpha;
-  float Wsuf;
-  float lr[3], lk[3];          // adjoint of the node state at the end of the step being reversed
-  float lkap, lte;             // partial adjoints of kappa and T_e at that node
-  // per-step adjoints handed from the transfer/tube part (A) and the
-  // neighbours (B) of step m to the central reverse (C) of the same step one
-  // iteration later; double-buffered by the parity of m
-  struct {
-    float lt[3], le1[3], le2[3], leps, lalpha;  // chord, basis and eps adjoints
-    float lpc[3];                                // the clip point (clipped last step)
-    float slp[3], slk[3];                        // sum of the neighbour seed adjoints
-  } st[2];
-  float lpos[3];               // value adjoint of the node A just completed
+#ifndef RT_ADJ_MIN_BLOCKS
+#define RT_ADJ_MIN_BLOCKS 4
+#endif
+constexpr int kAdjMinBlocks = RT_ADJ_MIN_BLOCKS;  // occupancy target (128-thread blocks)
+
+// One recomputed step of a segment (node m = m0 + j), in the thread's local
+// memory (the reverse reads it back last to first).
+struct StepRec {
+  float r[3], k[3], dr[3];     // node state and the chord increment of step m
+  float kap, te, ne, tau;      // node transfer values; optical depth at the node
+  float lns_next, lnm;         // ln S at node m+1 and ln M^{m+1}
+  float c1[3], c2[3];          // scaled separations of the +-e1, +-e2 pairs
 };
 
-#ifndef RT_ADJ_MIN_BLOCKS
-#define RT_ADJ_MIN_BLOCKS 5
-#endif
-constexpr int kAdjMinBlocks = RT_ADJ_MIN_BLOCKS;  // occupancy target: 5 x 128 threads per SM
-
-template <int NB>
-__global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_bundles(const __grid_constant__ AdjParams P) {
-  constexpr int L = NB + 1;
-  constexpr int BPW = 32 / L;
+// The adjoint of the forward (trace_rays), one thread per ray bundle.  Per
+// ray, segment by segment from the last: recompute the segment's K central
+// steps from its checkpoint with the forward's own step code (complete_step,
+// retrace_step), then reverse it step by step: (A) the transfer of the
+// segment and the tube area of the step (Eqs. 2, 9-12), (B) each
+// neighbour's retrace (RK4 stages 1-3), (C) the central RK4 step with its
+// chord, basis and eps (Eqs. 4-8).  Supported forms: step-wise with 4
+// neighbours, or magnification off (NB = 0).
+template <int NB, bool kMixed>
+__global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_rays(const __grid_constant__ AdjParams P) {
+  static_assert(NB == 0 || NB == 4, "adjoint: 4 step-wise neighbours or none");
   constexpr int K = kCkptEvery;
-  __shared__ AdjState S[kThreads / 32][BPW];
   const int lane = threadIdx.x & 31;
-  const int q = lane % L;
-  const bool used = (lane / L) < BPW;
-  const int base = used ? lane - q : lane;
-  const bool central = used && q == 0;
-  const int bundle = used ? lane / L : 0;
-  AdjState& A = S[threadIdx.x >> 5][bundle];
-  const long slot = ((long)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * BPW + bundle;
-  StepRec* R = P.rec + slot * (K + 1);
   const float h = P.h;
-  bool active = false, exhausted = !central;
+  StepRec R[K + 1];
+
+  // per-ray state of the reverse sweep
   unsigned int item = 0;
+  bool active = false, exhausted = false;
+  int N = 0, status = 0, seg = 0;
+  bool clipped = false;
+  float kf = 0.f, kn2 = 0.f, kap_c = 0.f, ln_f = 0.f, lamT = 0.f, alpha = 1.f;
+  float Wsuf = 0.f;                   // weight of everything beyond the node (sum of later terms)
+  Vec Lr{0.f, 0.f, 0.f}, Lk{0.f, 0.f, 0.f};  // adjoints of the node state (r, k)
+  float lkap = 0.f, lte = 0.f;        // partial adjoints of kappa and T_e at the node
 
   while (true) {
     // ---------------------------------------------------------- refill
-    bool need = central && !active && !exhausted;
+    bool need = !active && !exhausted;
     unsigned needmask = __ballot_sync(kFull, need);
     while (needmask) {
       const int leader = __ffs(needmask) - 1;
@@ -345,23 +354,24 @@ __global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_bundles(const
           const FreqDev& F = P.freq[fi];
           const size_t o = (size_t)F.out_slab * P.view.npix + pix;
           const RayDiag d = P.diag[o];
-          const float lamT = P.dL_dTb[o];
+          const float lw = P.dL_dTb[o];
           // the checkpoints were sized from a step count: it must be this ray's
-          const unsigned long long n_ck = (d.steps > 0) ? (unsigned long long)((d.steps - 1) / K + 1) : 0ull;
+          const unsigned long long n_ck =
+              (d.steps > 0 && lw != 0.f) ? (unsigned long long)((d.steps - 1) / K + 1) : 0ull;
           const bool fits = P.ck_off[item + 1] - P.ck_off[item] == n_ck;
           if (!fits) atomicAdd(P.mismatch, 1ull);
-          const bool has = fits && d.steps > 0 && d.status >= kExitOuter && d.status <= kStepLimit && lamT != 0.f;
-          if (has) {
-            A.N = d.steps;
-            A.status = d.status;
-            A.clipped = (d.status == kExitOuter || d.status == kHitInner) ? 1 : 0;
-            A.seg = (d.steps - 1) / K;
-            A.kf = F.kf; A.kn2 = F.kn2; A.kap_c = F.kap_c; A.ln_f = F.ln_f;
-            A.lamT = lamT;
-            A.alpha = 1.f;
-            A.Wsuf = 0.f;
-            A.lr[0] = A.lr[1] = A.lr[2] = A.lk[0] = A.lk[1] = A.lk[2] = 0.f;
-            A.lkap = A.lte = 0.f;
+          if (fits && d.steps > 0 && d.status >= kExitOuter && d.status <= kStepLimit && lw != 0.f) {
+            N = d.steps;
+            status = d.status;
+            clipped = (d.status == kExitOuter || d.status == kHitInner);
+            seg = (d.steps - 1) / K;
+            kf = F.kf; kn2 = F.kn2; kap_c = F.kap_c; ln_f = F.ln_f;
+            lamT = lw;
+            alpha = 1.f;
+            Wsuf = 0.f;
+            Lr = {0.f, 0.f, 0.f};
+            Lk = {0.f, 0.f, 0.f};
+            lkap = lte = 0.f;
             active = true;
             need = false;
           }
@@ -370,22 +380,15 @@ __global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_bundles(const
       needmask = __ballot_sync(kFull, need);
     }
     if (!__any_sync(kFull, active)) break;
+    if (!active) continue;
 
     // ---------------------------------------------- recompute the segment
-    // Pipelined as the forward: in iteration j the central lane steps node
-    // m0 + j while its neighbours retrace step m0 + j - 1 from the seeds
-    // broadcast one iteration earlier, all in one RK4 pass.
-    const int m0 = active ? A.seg * K : 0;
-    const int n_s = active ? min(K, A.N - m0) : 0;
-    const bool last_seg = active && (m0 + n_s == A.N);
-    const int ns_b = __shfl_sync(kFull, n_s, base);      // the bundle's segment length, on every lane
-    const int ns_w = __reduce_max_sync(kFull, ns_b);     // the warp's longest
-    float px = 0.f, py = 0.f, pz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
-    float rlx = 0.f, rly = 0.f, rlz = 0.f, klx = 0.f, kly = 0.f, klz = 0.f;
-    float tau = 0.f, lns = 0.f;
-    bool has_seed = false;  // neighbour lanes: a retrace is pending
-    if (central && active) {
-      const Ckpt& c = P.ckpt[P.ck_off[item] + A.seg];
+    const int m0 = seg * K;
+    const int n_s = min(K, N - m0);
+    const bool last_seg = (m0 + n_s == N);
+    float px, py, pz, kx, ky, kz, rlx, rly, rlz, klx, kly, klz, tau, lns;
+    {
+      const Ckpt& c = P.ckpt[P.ck_off[item] + seg];
       px = c.r[0]; py = c.r[1]; pz = c.r[2];
       kx = c.k[0]; ky = c.k[1]; kz = c.k[2];
       rlx = c.rl[0]; rly = c.rl[1]; rlz = c.rl[2];
@@ -393,338 +396,203 @@ __global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_bundles(const
       tau = c.tau_hi + c.tau_lo;
       lns = c.lns_hi + c.lns_lo;
     }
-    const float kf_lane = __shfl_sync(kFull, (central && active) ? A.kf : 0.f, base);
-    for (int j = 0; j <= ns_w; ++j) {
-      const bool cw = central && j < n_s;
-      Rk4Out o;
-      o.Gx = o.Gy = o.Gz = o.Ax = o.Ay = o.Az = 0.f;
-      o.ne1 = o.te1 = 0.f;
-      if (cw || (NB > 0 && has_seed)) o = rk4_step(P.G, kf_lane, h, px, py, pz, kx, ky, kz, cw);
+    for (int j = 0; j < n_s; ++j) {
+      const Rk4Out o = rk4_central(P.G, kf, h, px, py, pz, kx, ky, kz);
+      const float kap = P.emission ? kappa_vac(o.ne1, o.te1, kap_c, ln_f) : 0.f;
+      if (j > 0) tau += 0.5f * (R[j - 1].kap + kap) * P.hrsun;
+      StepRec& rc = R[j];
+      rc.r[0] = px; rc.r[1] = py; rc.r[2] = pz;
+      rc.k[0] = kx; rc.k[1] = ky; rc.k[2] = kz;
+      rc.kap = kap; rc.te = o.te1; rc.ne = o.ne1; rc.tau = tau;
+      Vec dr, rn, kn;
+      complete_step<kMixed>(h, P.h2_6, P.h_6, o, px, py, pz, kx, ky, kz, rlx, rly, rlz, klx, kly, klz, dr, rn, kn);
+      rc.dr[0] = dr.x; rc.dr[1] = dr.y; rc.dr[2] = dr.z;
       if (NB > 0) {
-        // separations of the retraced step m0 + j - 1: D_j = G_{+j} - G_{-j}
-        const float dx = o.Gx - __shfl_down_sync(kFull, o.Gx, 1);
-        const float dy = o.Gy - __shfl_down_sync(kFull, o.Gy, 1);
-        const float dz = o.Gz - __shfl_down_sync(kFull, o.Gz, 1);
-        const Vec d1{__shfl_sync(kFull, dx, base + 1), __shfl_sync(kFull, dy, base + 1), __shfl_sync(kFull, dz, base + 1)};
-        const Vec d2{__shfl_sync(kFull, dx, base + 3), __shfl_sync(kFull, dy, base + 3), __shfl_sync(kFull, dz, base + 3)};
-        if (central && j >= 1 && j - 1 < n_s) {
-          StepRec& rc = R[j - 1];
-          const float sc = P.h2_12 / rc.eps;
-          const Vec c1{sc * d1.x, sc * d1.y, sc * d1.z}, c2{sc * d2.x, sc * d2.y, sc * d2.z};
-          const Vec tp{rc.t[0], rc.t[1], rc.t[2]}, e1p{rc.e1[0], rc.e1[1], rc.e1[2]}, e2p{rc.e2[0], rc.e2[1], rc.e2[2]};
-          const float lm = ln_m(c1, c2, e1p, e2p, tp);
-          rc.c1[0] = c1.x; rc.c1[1] = c1.y; rc.c1[2] = c1.z;
-          rc.c2[0] = c2.x; rc.c2[1] = c2.y; rc.c2[2] = c2.z;
-          rc.lnm = lm;
-          lns += lm;
-          rc.lns_next = lns;
-        }
-      } else if (central && j >= 1 && j - 1 < n_s) {
-        R[j - 1].lnm = 0.f;
-        R[j - 1].lns_next = lns;
+        const Retrace T = retrace_step<(NB > 0 ? NB : 4)>(P.G, kf, h, P.h2_6, P.h2_12, P.eta, P.eps_fixed, px, py,
+                                                          pz, kx, ky, kz, dr, Vec{o.Gx, o.Gy, o.Gz});
+        rc.c1[0] = T.c1.x; rc.c1[1] = T.c1.y; rc.c1[2] = T.c1.z;
+        rc.c2[0] = T.c2.x; rc.c2[1] = T.c2.y; rc.c2[2] = T.c2.z;
+        rc.lnm = T.lm;
+        lns += T.lm;
+      } else {
+        rc.lnm = 0.f;
       }
-      Vec sr{0.f, 0.f, 0.f}, sk{0.f, 0.f, 0.f}, sa{0.f, 0.f, 0.f}, sb{0.f, 0.f, 0.f};
-      if (cw) {
-        const float kap = P.emission ? kappa_vac(o.ne1, o.te1, A.kap_c, A.ln_f) : 0.f;
-        if (j > 0) tau += 0.5f * (R[j - 1].kap + kap) * P.hrsun;
-        StepRec& rc = R[j];
-        rc.r[0] = px; rc.r[1] = py; rc.r[2] = pz;
-        rc.k[0] = kx; rc.k[1] = ky; rc.k[2] = kz;
-        rc.kap = kap; rc.te = o.te1; rc.ne = o.ne1; rc.tau = tau;
-        const Vec dr{fmaf(h, kx + klx, P.h2_6 * o.Gx), fmaf(h, ky + kly, P.h2_6 * o.Gy),
-                     fmaf(h, kz + klz, P.h2_6 * o.Gz)};
-        const Vec dk{P.h_6 * o.Ax, P.h_6 * o.Ay, P.h_6 * o.Az};
-        rc.dr[0] = dr.x; rc.dr[1] = dr.y; rc.dr[2] = dr.z;
-        const float d2n = dot3(dr, dr);
-        const float ids = rsqrtf(d2n);
-        const Vec tp{dr.x * ids, dr.y * ids, dr.z * ids};
-        rc.t[0] = tp.x; rc.t[1] = tp.y; rc.t[2] = tp.z;
-        if (NB > 0) {
-          Vec e1p, e2p;
-          basis(tp, e1p, e2p);
-          const float eps = (P.eps_fixed > 0.f) ? P.eps_fixed : P.eta * (d2n * ids);
-          rc.e1[0] = e1p.x; rc.e1[1] = e1p.y; rc.e1[2] = e1p.z;
-          rc.e2[0] = e2p.x; rc.e2[1] = e2p.y; rc.e2[2] = e2p.z;
-          rc.eps = eps;
-          rc.axis = (fabsf(tp.z) <= 0.9f) ? 0 : 1;
-          sr = {px, py, pz};
-          sk = {kx, ky, kz};
-          sa = {eps * e1p.x, eps * e1p.y, eps * e1p.z};
-          sb = {eps * e2p.x, eps * e2p.y, eps * e2p.z};
-        }
-        float e;
-        float nx, ny, nz;
-        fast_two_sum(px, dr.x + rlx, nx, e); rlx = e;
-        fast_two_sum(py, dr.y + rly, ny, e); rly = e;
-        fast_two_sum(pz, dr.z + rlz, nz, e); rlz = e;
-        px = nx; py = ny; pz = nz;
-        float mx, my, mz;
-        fast_two_sum(kx, dk.x + klx, mx, e); klx = e;
-        fast_two_sum(ky, dk.y + kly, my, e); kly = e;
-        fast_two_sum(kz, dk.z + klz, mz, e); klz = e;
-        kx = mx; ky = my; kz = mz;
-      }
-      if (NB > 0) {
-        // seeds of step m0 + j for the next iteration: +-eps e1 (roles 1, 2), +-eps e2 (3, 4)
-        const bool e = __shfl_sync(kFull, cw ? 1 : 0, base) != 0;
-        const float bx = __shfl_sync(kFull, sr.x, base), by = __shfl_sync(kFull, sr.y, base),
-                    bz = __shfl_sync(kFull, sr.z, base);
-        const float bkx = __shfl_sync(kFull, sk.x, base), bky = __shfl_sync(kFull, sk.y, base),
-                    bkz = __shfl_sync(kFull, sk.z, base);
-        const float ax = __shfl_sync(kFull, sa.x, base), ay = __shfl_sync(kFull, sa.y, base),
-                    az = __shfl_sync(kFull, sa.z, base);
-        const float cx = __shfl_sync(kFull, sb.x, base), cy = __shfl_sync(kFull, sb.y, base),
-                    cz = __shfl_sync(kFull, sb.z, base);
-        if (used && q > 0) {
-          has_seed = e;
-          const float sgn = (q & 1) ? 1.f : -1.f;
-          px = bx + sgn * ((q <= 2) ? ax : cx);
-          py = by + sgn * ((q <= 2) ? ay : cy);
-          pz = bz + sgn * ((q <= 2) ? az : cz);
-          kx = bkx; ky = bky; kz = bkz;
-        }
-      }
+      rc.lns_next = lns;
+      px = rn.x; py = rn.y; pz = rn.z;
+      kx = kn.x; ky = kn.y; kz = kn.z;
     }
-    // the closing node of the segment: node m0 + n_s (the clip point on a clipped final step)
-    if (central && active) {
+    // the closing node of the segment: node m0 + n_s (the crossing point on a clipped last step)
+    {
       StepRec& rl = R[n_s];
       float qx = px, qy = py, qz = pz;
-      if (last_seg && A.clipped) {
+      if (last_seg && clipped) {
         const StepRec& rp = R[n_s - 1];
         const Vec rr{rp.r[0], rp.r[1], rp.r[2]}, dr{rp.dr[0], rp.dr[1], rp.dr[2]};
-        const float a = (A.status == kHitInner) ? chord_crossing(rr, dr, P.G.r_min, false)
-                                                 : chord_crossing(rr, dr, P.G.r_max, true);
-        A.alpha = a;
+        const float a = (status == kHitInner) ? chord_crossing(rr, dr, P.G.r_min, false)
+                                              : chord_crossing(rr, dr, P.G.r_max, true);
+        alpha = a;
         qx = fmaf(a, dr.x, rr.x); qy = fmaf(a, dr.y, rr.y); qz = fmaf(a, dr.z, rr.z);
       }
-      const Sample s = eval_field(P.G, qx, qy, qz, true);
-      const float kap = P.emission ? kappa_vac(s.ne, s.te, A.kap_c, A.ln_f) : 0.f;
+      const Sample s = eval_field_t<true>(P.G, qx, qy, qz, true);
+      const float kap = P.emission ? kappa_vac(s.ne, s.te, kap_c, ln_f) : 0.f;
       rl.r[0] = qx; rl.r[1] = qy; rl.r[2] = qz;
       rl.kap = kap; rl.te = s.te; rl.ne = s.ne;
       if (last_seg) {
-        const float alpha = A.clipped ? A.alpha : 1.f;
-        const float tauN = tau + 0.5f * (R[n_s - 1].kap + kap) * P.hrsun * alpha;
+        const float al = clipped ? alpha : 1.f;
+        const float tauN = tau + 0.5f * (R[n_s - 1].kap + kap) * P.hrsun * al;
         rl.tau = tauN;
         const float sN = __expf(lns - tauN);
         float tbc = 0.f;
-        if (A.status == kHitInner) tbc = (P.tbc_mode == 1) ? P.tbc_K : s.te;
-        A.Wsuf = tbc * sN;  // the boundary term
-        if (A.status == kHitInner && P.tbc_mode == 0) A.lte = A.lamT * sN;
+        if (status == kHitInner) tbc = (P.tbc_mode == 1) ? P.tbc_K : s.te;
+        Wsuf = tbc * sN;  // the boundary term
+        if (status == kHitInner && P.tbc_mode == 0) lte = lamT * sN;
       }
     }
 
     // ------------------------------------------------ reverse the segment
-    // Pipelined: in iteration t the central lane runs the transfer and
-    // tube-area adjoint of step m0 + t (A) and the reverse of its own RK4
-    // step m0 + t + 1 (C), while its neighbours reverse their retrace of step
-    // m0 + t (B); B and C share one rk4_reverse pass.  C of step t + 1 needs
-    // A and B of step t + 1, which the previous iteration left in the
-    // bundle's shared state.
-    for (int t = ns_w - 1; t >= -1; --t) {
-      const bool a_ok = central && t >= 0 && t < n_s;
-      const bool c_ok = central && t + 1 < n_s;
-      const bool b_ok = NB > 0 && used && q > 0 && t >= 0 && t < ns_b;
-      // A: transfer of segment m = m0 + t (Eq. 2 front to back, differentiated)
-      float lD1x = 0.f, lD1y = 0.f, lD1z = 0.f, lD2x = 0.f, lD2y = 0.f, lD2z = 0.f;
-      if (a_ok) {
-        auto& S = A.st[t & 1];
-        const bool last_step = last_seg && t == n_s - 1;
-        const StepRec& rc = R[t];
-        const StepRec& rn = R[t + 1];
-        const float alpha = (last_step && A.clipped) ? A.alpha : 1.f;
-        const float kap_sum = rc.kap + rn.kap;
-        const float dt = 0.5f * kap_sum * P.hrsun * alpha;
-        const float tbar = 0.5f * (rc.te + rn.te);
-        const float qv = __expf(rc.lns_next - rc.tau);
-        const float ed = __expf(-dt);
-        const float om = one_minus_exp_neg(dt);
-        const float W = tbar * om * qv;
-        const float lDt = A.lamT * (tbar * ed * qv - A.Wsuf);
-        const float lTbar = A.lamT * om * qv;
-        const float lLnM = A.lamT * (W + A.Wsuf);
-        A.Wsuf += W;
-        const float lk_node = 0.5f * P.hrsun * alpha * lDt;
-        const float lkap_n = A.lkap + lk_node;
-        const float lte_n = A.lte + 0.5f * lTbar;
-        S.lalpha = 0.5f * kap_sum * P.hrsun * lDt;
-        // node m+1 is complete: scatter its value adjoints
-        float dkn, dkt;
-        kappa_partials(rn.ne, rn.te, A.kap_c, A.ln_f, dkn, dkt);
-        if (!P.emission) { dkn = 0.f; dkt = 0.f; }
-        const Vec lpos = value_adjoint(P.G, rn.r[0], rn.r[1], rn.r[2], lkap_n * dkn, lte_n + lkap_n * dkt,
-                                       P.dne, P.dte);
-        if (last_step && A.clipped) {
-          S.lpc[0] = lpos.x; S.lpc[1] = lpos.y; S.lpc[2] = lpos.z;
-          A.lpos[0] = A.lpos[1] = A.lpos[2] = 0.f;
-        } else {
-          A.lpos[0] = lpos.x; A.lpos[1] = lpos.y; A.lpos[2] = lpos.z;
-        }
-        A.lkap = lk_node;  // node m, completed by segment m - 1
-        A.lte = 0.5f * lTbar;
-        // tube area of step m (Eqs. 9-11, differentiated); the neighbour
-        // seeds add their parts after B
-        S.lt[0] = S.lt[1] = S.lt[2] = 0.f;
-        S.le1[0] = S.le1[1] = S.le1[2] = 0.f;
-        S.le2[0] = S.le2[1] = S.le2[2] = 0.f;
-        S.leps = 0.f;
-        S.slp[0] = S.slp[1] = S.slp[2] = S.slk[0] = S.slk[1] = S.slk[2] = 0.f;
-        if (NB > 0) {
-          const Vec c1{rc.c1[0], rc.c1[1], rc.c1[2]}, c2{rc.c2[0], rc.c2[1], rc.c2[2]};
-          const Vec t3{rc.t[0], rc.t[1], rc.t[2]}, e1{rc.e1[0], rc.e1[1], rc.e1[2]}, e2{rc.e2[0], rc.e2[1], rc.e2[2]};
-          const float lm1 = lLnM * __expf(-rc.lnm);  // d ln(1 + m1) / d m1 = 1 / M
-          const Vec c2xt{c2.y * t3.z - c2.z * t3.y, c2.z * t3.x - c2.x * t3.z, c2.x * t3.y - c2.y * t3.x};
-          const Vec txc1{t3.y * c1.z - t3.z * c1.y, t3.z * c1.x - t3.x * c1.z, t3.x * c1.y - t3.y * c1.x};
-          const Vec lc1{lm1 * (e1.x + c2xt.x), lm1 * (e1.y + c2xt.y), lm1 * (e1.z + c2xt.z)};
-          const Vec lc2{lm1 * (e2.x + txc1.x), lm1 * (e2.y + txc1.y), lm1 * (e2.z + txc1.z)};
-          S.le1[0] = lm1 * c1.x; S.le1[1] = lm1 * c1.y; S.le1[2] = lm1 * c1.z;
-          S.le2[0] = lm1 * c2.x; S.le2[1] = lm1 * c2.y; S.le2[2] = lm1 * c2.z;
-          S.lt[0] = lm1 * (c1.y * c2.z - c1.z * c2.y);
-          S.lt[1] = lm1 * (c1.z * c2.x - c1.x * c2.z);
-          S.lt[2] = lm1 * (c1.x * c2.y - c1.y * c2.x);
-          S.leps = -(dot3(c1, lc1) + dot3(c2, lc2)) / rc.eps;
-          const float sc = P.h2_12 / rc.eps;
-          lD1x = sc * lc1.x; lD1y = sc * lc1.y; lD1z = sc * lc1.z;
-          lD2x = sc * lc2.x; lD2y = sc * lc2.y; lD2z = sc * lc2.z;
-        }
-      } else if (central) {
-        A.lpos[0] = A.lpos[1] = A.lpos[2] = 0.f;
+    for (int t = n_s - 1; t >= 0; --t) {
+      const StepRec& rc = R[t];
+      const StepRec& rn = R[t + 1];
+      const bool last_step = last_seg && t == n_s - 1;
+      const bool clip = last_step && clipped;
+      // (A) transfer of segment m = m0 + t (Eq. 2 front to back, differentiated)
+      const float al = clip ? alpha : 1.f;
+      const float kap_sum = rc.kap + rn.kap;
+      const float dt = 0.5f * kap_sum * P.hrsun * al;
+      const float tbar = 0.5f * (rc.te + rn.te);
+      const float qv = __expf(rc.lns_next - rc.tau);
+      const float ed = __expf(-dt);
+      const float om = one_minus_exp_neg(dt);
+      const float W = tbar * om * qv;
+      const float lDt = lamT * (tbar * ed * qv - Wsuf);
+      const float lTbar = lamT * om * qv;
+      const float lLnM = lamT * (W + Wsuf);
+      Wsuf += W;
+      const float lk_node = 0.5f * P.hrsun * al * lDt;
+      const float lkap_n = lkap + lk_node;
+      const float lte_n = lte + 0.5f * lTbar;
+      const float lalpha = 0.5f * kap_sum * P.hrsun * lDt;
+      // node m+1 is complete: scatter its value adjoints
+      float dkn, dkt;
+      kappa_partials(rn.ne, rn.te, kap_c, ln_f, dkn, dkt);
+      if (!P.emission) { dkn = 0.f; dkt = 0.f; }
+      const Vec lpos = value_adjoint(P.G, rn.r[0], rn.r[1], rn.r[2], lkap_n * dkn, lte_n + lkap_n * dkt, P.dne, P.dte);
+      Vec lpc{0.f, 0.f, 0.f};
+      if (clip) {
+        lpc = lpos;   // the crossing point closes the path
+      } else {
+        Lr = {Lr.x + lpos.x, Lr.y + lpos.y, Lr.z + lpos.z};  // node m+1's full adjoint
       }
-      // B and C in one rk4_reverse pass: the neighbours reverse their
-      // retrace of step t (G enters the separations only), the central lane
-      // its own step t + 1
-      Vec rp{0.f, 0.f, 0.f}, rk{0.f, 0.f, 0.f}, lr_in{0.f, 0.f, 0.f}, lk_in{0.f, 0.f, 0.f}, lg{0.f, 0.f, 0.f};
-      Vec lp_o{0.f, 0.f, 0.f}, lk_o{0.f, 0.f, 0.f};
+      lkap = lk_node;  // node m, completed by segment m - 1
+      lte = 0.5f * lTbar;
+
+      // tube area of step m (Eqs. 9-11, differentiated) and (B) the neighbours
+      const Vec dr{rc.dr[0], rc.dr[1], rc.dr[2]};
+      Vec slp{0.f, 0.f, 0.f}, slk{0.f, 0.f, 0.f};   // sums of the seed adjoints
+      Vec lt{0.f, 0.f, 0.f}, le1{0.f, 0.f, 0.f}, le2{0.f, 0.f, 0.f};
+      float leps = 0.f;
+      Vec t3{0.f, 0.f, 0.f}, e1{0.f, 0.f, 0.f}, e2{0.f, 0.f, 0.f};
+      float eps = 0.f;
       if (NB > 0) {
-        const float g1x = __shfl_sync(kFull, lD1x, base), g1y = __shfl_sync(kFull, lD1y, base),
-                    g1z = __shfl_sync(kFull, lD1z, base);
-        const float g2x = __shfl_sync(kFull, lD2x, base), g2y = __shfl_sync(kFull, lD2y, base),
-                    g2z = __shfl_sync(kFull, lD2z, base);
-        if (b_ok) {
-          const StepRec& rc = R[t];
-          const float sgn = (q & 1) ? 1.f : -1.f;
-          const bool first = q <= 2;
-          const float* ev = first ? rc.e1 : rc.e2;
-          rp = {rc.r[0] + sgn * rc.eps * ev[0], rc.r[1] + sgn * rc.eps * ev[1], rc.r[2] + sgn * rc.eps * ev[2]};
-          rk = {rc.k[0], rc.k[1], rc.k[2]};
-          lg = first ? Vec{sgn * g1x, sgn * g1y, sgn * g1z} : Vec{sgn * g2x, sgn * g2y, sgn * g2z};
+        const float d2n = dot3(dr, dr);
+        const float ids = rsqrtf(d2n);
+        t3 = {dr.x * ids, dr.y * ids, dr.z * ids};
+        basis(t3, e1, e2);
+        eps = (P.eps_fixed > 0.f) ? P.eps_fixed : P.eta * (d2n * ids);
+        const Vec c1{rc.c1[0], rc.c1[1], rc.c1[2]}, c2{rc.c2[0], rc.c2[1], rc.c2[2]};
+        const float lm1 = lLnM * __expf(-rc.lnm);  // d ln(1 + m1) / d m1 = 1 / M
+        const Vec c2xt{c2.y * t3.z - c2.z * t3.y, c2.z * t3.x - c2.x * t3.z, c2.x * t3.y - c2.y * t3.x};
+        const Vec txc1{t3.y * c1.z - t3.z * c1.y, t3.z * c1.x - t3.x * c1.z, t3.x * c1.y - t3.y * c1.x};
+        const Vec lc1{lm1 * (e1.x + c2xt.x), lm1 * (e1.y + c2xt.y), lm1 * (e1.z + c2xt.z)};
+        const Vec lc2{lm1 * (e2.x + txc1.x), lm1 * (e2.y + txc1.y), lm1 * (e2.z + txc1.z)};
+        le1 = {lm1 * c1.x, lm1 * c1.y, lm1 * c1.z};
+        le2 = {lm1 * c2.x, lm1 * c2.y, lm1 * c2.z};
+        lt = {lm1 * (c1.y * c2.z - c1.z * c2.y), lm1 * (c1.z * c2.x - c1.x * c2.z), lm1 * (c1.x * c2.y - c1.y * c2.x)};
+        leps = -(dot3(c1, lc1) + dot3(c2, lc2)) / eps;
+        const float sc = P.h2_12 / eps;
+        const Vec rk{rc.k[0], rc.k[1], rc.k[2]};
+        // seeds r_m +- eps e_j with k = k_m; G of a "+" seed enters D_j with +, of a "-" seed with -
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+          const bool first = q < 2;
+          const float sgn = (q & 1) ? -1.f : 1.f;
+          const Vec ev = first ? e1 : e2;
+          const Vec lc = first ? lc1 : lc2;
+          const Vec seed{rc.r[0] + sgn * eps * ev.x, rc.r[1] + sgn * eps * ev.y, rc.r[2] + sgn * eps * ev.z};
+          const Vec lg{sgn * sc * lc.x, sgn * sc * lc.y, sgn * sc * lc.z};
+          Vec lps{0.f, 0.f, 0.f}, lks{0.f, 0.f, 0.f};
+          rk4_g3_reverse(P.G, kf, h, seed, rk, lg, lps, lks, P.dne);
+          slp = {slp.x + lps.x, slp.y + lps.y, slp.z + lps.z};
+          slk = {slk.x + lks.x, slk.y + lks.y, slk.z + lks.z};
+          leps += sgn * dot3(ev, lps);
+          if (first) le1 = {fmaf(sgn * eps, lps.x, le1.x), fmaf(sgn * eps, lps.y, le1.y), fmaf(sgn * eps, lps.z, le1.z)};
+          else le2 = {fmaf(sgn * eps, lps.x, le2.x), fmaf(sgn * eps, lps.y, le2.y), fmaf(sgn * eps, lps.z, le2.z)};
         }
       }
-      if (c_ok) {
-        // C's inputs: the output adjoints of central step t + 1 and its seed/chord terms
-        const auto& S = A.st[(t + 1) & 1];
-        const bool last_step = last_seg && t + 1 == n_s - 1;
-        const StepRec& rc = R[t + 1];
-        Vec ldr{0.f, 0.f, 0.f};
-        if (NB > 0) {
-          const Vec e1{rc.e1[0], rc.e1[1], rc.e1[2]}, t3{rc.t[0], rc.t[1], rc.t[2]};
-          lp_o = {S.slp[0], S.slp[1], S.slp[2]};
-          lk_o = {S.slk[0], S.slk[1], S.slk[2]};
-          Vec le1{S.le1[0], S.le1[1], S.le1[2]}, lt{S.lt[0], S.lt[1], S.lt[2]};
-          const Vec le2{S.le2[0], S.le2[1], S.le2[2]};
-          // e2 = t x e1
-          lt = {lt.x + (e1.y * le2.z - e1.z * le2.y), lt.y + (e1.z * le2.x - e1.x * le2.z),
-                lt.z + (e1.x * le2.y - e1.y * le2.x)};
-          le1 = {le1.x + (le2.y * t3.z - le2.z * t3.y), le1.y + (le2.z * t3.x - le2.x * t3.z),
-                 le1.z + (le2.x * t3.y - le2.y * t3.x)};
-          // e1 = c / |c|, c = a x t
-          const Vec av = (rc.axis == 0) ? Vec{0.f, 0.f, 1.f} : Vec{0.f, 1.f, 0.f};
-          const Vec cv{av.y * t3.z - av.z * t3.y, av.z * t3.x - av.x * t3.z, av.x * t3.y - av.y * t3.x};
-          const float ic = rsqrtf(dot3(cv, cv));
-          const float pe = dot3(e1, le1);
-          const Vec lc{(le1.x - pe * e1.x) * ic, (le1.y - pe * e1.y) * ic, (le1.z - pe * e1.z) * ic};
-          lt = {lt.x + (lc.y * av.z - lc.z * av.y), lt.y + (lc.z * av.x - lc.x * av.z),
-                lt.z + (lc.x * av.y - lc.y * av.x)};
-          // eps = eta |dr| (Eq. 8); t = dr / |dr| (Eq. 5)
-          const Vec dr{rc.dr[0], rc.dr[1], rc.dr[2]};
-          const float ids = rsqrtf(dot3(dr, dr));
-          const float lds = (P.eps_fixed > 0.f) ? 0.f : P.eta * S.leps;
-          const float pt = dot3(t3, lt);
-          ldr = {(lt.x - pt * t3.x) * ids + t3.x * lds, (lt.y - pt * t3.y) * ids + t3.y * lds,
-                 (lt.z - pt * t3.z) * ids + t3.z * lds};
-        }
-        Vec lr_next{A.lr[0], A.lr[1], A.lr[2]};
-        if (last_step && A.clipped) {
-          // clip point pc = r_m + alpha dr with |pc| = R: d alpha = -(pc . (d r_m + alpha d dr)) / (pc . dr)
-          const StepRec& rn = R[t + 2];
-          const Vec pc{rn.r[0], rn.r[1], rn.r[2]}, dr{rc.dr[0], rc.dr[1], rc.dr[2]};
-          const Vec lpc{S.lpc[0], S.lpc[1], S.lpc[2]};
-          const float den = dot3(pc, dr);
-          const float la = S.lalpha + dot3(lpc, dr);
-          const float g = (den != 0.f) ? la / den : 0.f;
-          lp_o = {lp_o.x + lpc.x - g * pc.x, lp_o.y + lpc.y - g * pc.y, lp_o.z + lpc.z - g * pc.z};
-          ldr = {ldr.x + A.alpha * (lpc.x - g * pc.x), ldr.y + A.alpha * (lpc.y - g * pc.y),
-                 ldr.z + A.alpha * (lpc.z - g * pc.z)};
-          lr_next = {0.f, 0.f, 0.f};  // the unclipped node is used only through the chord
-        }
-        // dr = r' - r_m
-        lr_in = {lr_next.x + ldr.x, lr_next.y + ldr.y, lr_next.z + ldr.z};
-        lp_o = {lp_o.x - ldr.x, lp_o.y - ldr.y, lp_o.z - ldr.z};
-        lk_in = {A.lk[0], A.lk[1], A.lk[2]};
-        rp = {rc.r[0], rc.r[1], rc.r[2]};
-        rk = {rc.k[0], rc.k[1], rc.k[2]};
-      }
-      if (c_ok || b_ok) rk4_reverse(P.G, kf_lane, h, rp, rk, lr_in, lk_in, lg, lp_o, lk_o, P.dne);
-      // gather the neighbours' seed adjoints of step t to the central lane
+
+      // (C) the central RK4 step m with its chord, basis and eps
+      Vec ldr{0.f, 0.f, 0.f};
       if (NB > 0) {
-        Vec lps[4], lks[4];
-#pragma unroll
-        for (int n = 0; n < 4; ++n) {
-          const int src = base + 1 + n;
-          lps[n] = {__shfl_sync(kFull, lp_o.x, src), __shfl_sync(kFull, lp_o.y, src), __shfl_sync(kFull, lp_o.z, src)};
-          lks[n] = {__shfl_sync(kFull, lk_o.x, src), __shfl_sync(kFull, lk_o.y, src), __shfl_sync(kFull, lk_o.z, src)};
-        }
-        if (a_ok) {
-          // seeds r_m +- eps e_j with k = k_m: node, eps and basis adjoints of step t
-          auto& S = A.st[t & 1];
-          const StepRec& rc = R[t];
-          const Vec e1{rc.e1[0], rc.e1[1], rc.e1[2]}, e2{rc.e2[0], rc.e2[1], rc.e2[2]};
-#pragma unroll
-          for (int n = 0; n < 4; ++n) {
-            S.slp[0] += lps[n].x; S.slp[1] += lps[n].y; S.slp[2] += lps[n].z;
-            S.slk[0] += lks[n].x; S.slk[1] += lks[n].y; S.slk[2] += lks[n].z;
-          }
-          S.leps += dot3(e1, lps[0]) - dot3(e1, lps[1]) + dot3(e2, lps[2]) - dot3(e2, lps[3]);
-          S.le1[0] += rc.eps * (lps[0].x - lps[1].x);
-          S.le1[1] += rc.eps * (lps[0].y - lps[1].y);
-          S.le1[2] += rc.eps * (lps[0].z - lps[1].z);
-          S.le2[0] += rc.eps * (lps[2].x - lps[3].x);
-          S.le2[1] += rc.eps * (lps[2].y - lps[3].y);
-          S.le2[2] += rc.eps * (lps[2].z - lps[3].z);
-        }
+        // e2 = t x e1
+        lt = {lt.x + (e1.y * le2.z - e1.z * le2.y), lt.y + (e1.z * le2.x - e1.x * le2.z),
+              lt.z + (e1.x * le2.y - e1.y * le2.x)};
+        le1 = {le1.x + (le2.y * t3.z - le2.z * t3.y), le1.y + (le2.z * t3.x - le2.x * t3.z),
+               le1.z + (le2.x * t3.y - le2.y * t3.x)};
+        // e1 = c / |c|, c = a x t
+        const Vec av = (fabsf(t3.z) <= 0.9f) ? Vec{0.f, 0.f, 1.f} : Vec{0.f, 1.f, 0.f};
+        const Vec cv{av.y * t3.z - av.z * t3.y, av.z * t3.x - av.x * t3.z, av.x * t3.y - av.y * t3.x};
+        const float ic = rsqrtf(dot3(cv, cv));
+        const float pe = dot3(e1, le1);
+        const Vec lc{(le1.x - pe * e1.x) * ic, (le1.y - pe * e1.y) * ic, (le1.z - pe * e1.z) * ic};
+        lt = {lt.x + (lc.y * av.z - lc.z * av.y), lt.y + (lc.z * av.x - lc.x * av.z),
+              lt.z + (lc.x * av.y - lc.y * av.x)};
+        // eps = eta |dr| (Eq. 8); t = dr / |dr| (Eq. 5)
+        const float ids = rsqrtf(dot3(dr, dr));
+        const float lds = (P.eps_fixed > 0.f) ? 0.f : P.eta * leps;
+        const float pt = dot3(t3, lt);
+        ldr = {(lt.x - pt * t3.x) * ids + t3.x * lds, (lt.y - pt * t3.y) * ids + t3.y * lds,
+               (lt.z - pt * t3.z) * ids + t3.z * lds};
       }
-      // the adjoints at node m0 + t + 1: C's output plus A's value term
-      if (c_ok) {
-        A.lr[0] = lp_o.x + A.lpos[0]; A.lr[1] = lp_o.y + A.lpos[1]; A.lr[2] = lp_o.z + A.lpos[2];
-        A.lk[0] = lk_o.x; A.lk[1] = lk_o.y; A.lk[2] = lk_o.z;
-      } else if (a_ok) {
-        A.lr[0] += A.lpos[0]; A.lr[1] += A.lpos[1]; A.lr[2] += A.lpos[2];
+      Vec lp_o = slp, lk_o = slk;
+      Vec lr_next = Lr;
+      if (clip) {
+        // crossing point pc = r_m + alpha dr with |pc| = R: d alpha = -(pc . (d r_m + alpha d dr)) / (pc . dr)
+        const Vec pc{rn.r[0], rn.r[1], rn.r[2]};
+        const float den = dot3(pc, dr);
+        const float la = lalpha + dot3(lpc, dr);
+        const float g = (den != 0.f) ? la / den : 0.f;
+        lp_o = {lp_o.x + lpc.x - g * pc.x, lp_o.y + lpc.y - g * pc.y, lp_o.z + lpc.z - g * pc.z};
+        ldr = {ldr.x + alpha * (lpc.x - g * pc.x), ldr.y + alpha * (lpc.y - g * pc.y),
+               ldr.z + alpha * (lpc.z - g * pc.z)};
+        lr_next = {0.f, 0.f, 0.f};  // the unclipped node is used only through the chord
       }
+      // dr = r' - r_m
+      const Vec lr_in{lr_next.x + ldr.x, lr_next.y + ldr.y, lr_next.z + ldr.z};
+      lp_o = {lp_o.x - ldr.x, lp_o.y - ldr.y, lp_o.z - ldr.z};
+      rk4_reverse(P.G, kf, h, Vec{rc.r[0], rc.r[1], rc.r[2]}, Vec{rc.k[0], rc.k[1], rc.k[2]}, lr_in, Lk,
+                  Vec{0.f, 0.f, 0.f}, lp_o, lk_o, P.dne);
+      Lr = lp_o;  // node m (its value adjoint joins in the next step back)
+      Lk = lk_o;
     }
 
     // ------------------------------------------------ next segment / launch
-    if (central && active) {
-      if (A.seg == 0) {
-        // node 0 on the outer sphere: its transfer values and k0 = n(r0) (-o)
-        const StepRec& r0 = R[0];
-        float dkn, dkt;
-        kappa_partials(r0.ne, r0.te, A.kap_c, A.ln_f, dkn, dkt);
-        if (!P.emission) { dkn = 0.f; dkt = 0.f; }
-        float lam_ne = A.lkap * dkn;
-        const float lam_te = A.lte + A.lkap * dkt;
-        const Vec k0{r0.k[0], r0.k[1], r0.k[2]};
-        const float n0 = sqrtf(dot3(k0, k0));
-        if (n0 > 0.f) {
-          const float ln0 = (A.lk[0] * k0.x + A.lk[1] * k0.y + A.lk[2] * k0.z) / n0;
-          lam_ne += ln0 * A.kn2 / (2.f * n0);
-        }
-        value_adjoint(P.G, r0.r[0], r0.r[1], r0.r[2], lam_ne, lam_te, P.dne, P.dte);
-        active = false;
-      } else {
-        A.seg -= 1;
-      }
+    if (seg == 0) {
+      // node 0 on the outer sphere: its transfer values and k0 = n(r0) (-o)
+      const StepRec& r0 = R[0];
+      float dkn, dkt;
+      kappa_partials(r0.ne, r0.te, kap_c, ln_f, dkn, dkt);
+      if (!P.emission) { dkn = 0.f; dkt = 0.f; }
+      float lam_ne = lkap * dkn;
+      const float lam_te = lte + lkap * dkt;
+      const Vec k0{r0.k[0], r0.k[1], r0.k[2]};
+      const float n0 = sqrtf(dot3(k0, k0));
+      if (n0 > 0.f) lam_ne += dot3(Lk, k0) / n0 * kn2 / (2.f * n0);
+      value_adjoint(P.G, r0.r[0], r0.r[1], r0.r[2], lam_ne, lam_te, P.dne, P.dte);
+      active = false;
+    } else {
+      seg -= 1;
     }
   }
 }
 
 }  // namespace rt
-

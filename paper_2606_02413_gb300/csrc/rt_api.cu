@@ -194,12 +194,13 @@ int blocks_per_sm() {
   return cached;
 }
 
-template <int NB>
+template <int NB, bool M>
 int adj_blocks_per_sm() {
   static int cached = -1;
   if (cached < 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, adjoint_bundles<NB>, kThreads, 0) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, adjoint_rays<NB, M>, kThreads, 0) != cudaSuccess || b < 1)
+      b = 1;
     cached = b;
   }
   return cached;
@@ -862,12 +863,10 @@ rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const dou
   RayDiag* diag = nullptr;
   unsigned long long* ck_off = nullptr;
   Ckpt* ckpt = nullptr;
-  StepRec* rec = nullptr;
   auto release = [&]() {
     cudaFree(diag);
     cudaFree(ck_off);
     cudaFree(ckpt);
-    cudaFree(rec);
     if (!tb_out) cudaFree(tb);
   };
   cudaError_t e = cudaMalloc(&diag, sizeof(RayDiag) * total);
@@ -895,6 +894,7 @@ rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const dou
   P.counter = ctx->d_counter;
   P.stats = ctx->d_stats;
   P.total = (unsigned int)total;
+  P.skip_zero = dL_dTb;
   auto run_forward = [&]() -> cudaError_t {
     cudaError_t r = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), s);
     if (r == cudaSuccess) r = cudaMemsetAsync(ctx->d_stats, 0, 2 * sizeof(unsigned long long), s);
@@ -914,18 +914,28 @@ rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const dou
     release();
     return fail(RT_ERR_CUDA, "rt_backward (forward): %s", cudaGetErrorString(e));
   }
-  // checkpoint offsets, indexed by ticket (frequency in processing order, pixel)
+  // checkpoint offsets, indexed by ticket (frequency in processing order,
+  // pixel); a ray with dL/dT_b = 0 is not traced again and holds none
+  std::vector<float> hw(total);
+  e = cudaMemcpyAsync(hw.data(), dL_dTb, sizeof(float) * total, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    release();
+    return fail(RT_ERR_CUDA, "rt_backward (weights): %s", cudaGetErrorString(e));
+  }
   std::vector<unsigned long long> off(total + 1, 0);
   for (long t = 0; t < total; ++t) {
     const long fi = t / npix, pix = t - fi * npix;
-    const RayDiag& d = hd[(size_t)order[fi] * npix + pix];
-    const unsigned long long cnt = (d.steps > 0) ? (unsigned long long)((d.steps - 1) / kCkptEvery + 1) : 0ull;
+    const size_t o = (size_t)order[fi] * npix + pix;
+    const RayDiag& d = hd[o];
+    const unsigned long long cnt =
+        (d.steps > 0 && hw[o] != 0.f) ? (unsigned long long)((d.steps - 1) / kCkptEvery + 1) : 0ull;
     off[t + 1] = off[t] + cnt;
   }
-  const int grid_blocks = ctx->sm_count * (nb == 0 ? adj_blocks_per_sm<0>() : adj_blocks_per_sm<4>());
-  const long slots = (long)grid_blocks * (kThreads / 32) * (32 / (nb + 1));
+  const int per_sm = (nb == 0) ? (mixed ? adj_blocks_per_sm<0, true>() : adj_blocks_per_sm<0, false>())
+                               : (mixed ? adj_blocks_per_sm<4, true>() : adj_blocks_per_sm<4, false>());
+  const int grid_blocks = ctx->sm_count * per_sm;
   e = cudaMalloc(&ckpt, sizeof(Ckpt) * std::max<unsigned long long>(off[total], 1ull));
-  if (e == cudaSuccess) e = cudaMalloc(&rec, sizeof(StepRec) * slots * (kCkptEvery + 1));
   if (e == cudaSuccess) e = cudaMemcpyAsync(ck_off, off.data(), sizeof(unsigned long long) * (total + 1),
                                             cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ck_off + total + 1, 0, sizeof(unsigned long long), s);
@@ -950,14 +960,18 @@ rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const dou
     A.dL_dTb = dL_dTb;
     A.ckpt = ckpt;
     A.ck_off = ck_off;
-    A.rec = rec;
     A.dne = dL_dne;
     A.dte = dL_dte;
     A.counter = ctx->d_counter;
     A.total = (unsigned int)total;
     A.mismatch = ck_off + total + 1;
-    if (nb == 0) adjoint_bundles<0><<<grid_blocks, kThreads, 0, s>>>(A);
-    else adjoint_bundles<4><<<grid_blocks, kThreads, 0, s>>>(A);
+    if (nb == 0) {
+      if (mixed) adjoint_rays<0, true><<<grid_blocks, kThreads, 0, s>>>(A);
+      else adjoint_rays<0, false><<<grid_blocks, kThreads, 0, s>>>(A);
+    } else {
+      if (mixed) adjoint_rays<4, true><<<grid_blocks, kThreads, 0, s>>>(A);
+      else adjoint_rays<4, false><<<grid_blocks, kThreads, 0, s>>>(A);
+    }
     e = cudaGetLastError();
   }
   unsigned long long mismatch = 0;

@@ -116,6 +116,11 @@ __device__ __forceinline__ RayStart start_ray(const TraceParams& P, unsigned int
     const size_t o = (size_t)s.F->out_slab * P.view.npix + pix;
     s.out = P.tb_out + o;
     s.dg = P.diag ? P.diag + o : nullptr;
+    if (s.valid && P.skip_zero && P.skip_zero[o] == 0.f) {  // not traced: T_b 0, zero diagnostics
+      *s.out = 0.f;
+      if (s.dg) *s.dg = RayDiag{{0.f, 0.f, 0.f}, 0.f, 0.f, 0, 0};
+      s.valid = false;
+    }
   }
   s.enter = false;
   s.px = s.py = s.pz = s.kx = s.ky = s.kz = 0.f;

@@ -557,6 +557,10 @@ struct TraceParams {
   // optional checkpoints (image mode): ray t owns ckpt[ck_off[t] .. ck_off[t+1])
   Ckpt* ckpt;
   const unsigned long long* ck_off;
+  // optional (image mode): rays whose weight here is exactly 0 are not traced
+  // (T_b 0, diagnostics zero); the adjoint's passes skip rays that cannot
+  // contribute to the gradient
+  const float* skip_zero;
 };
 
 }  // namespace rt

@@ -97,6 +97,92 @@ __device__ __forceinline__ Vec pair_offset(int j, const Vec& a, const Vec& b) {
   return {s2 * (b.x - a.x), s2 * (b.y - a.y), s2 * (b.z - a.z)};
 }
 
+// Completes a central RK4 step from node (p, k) (Eq. 4 in increment form):
+// the chord dr = h (k + kl) + h^2/6 G, dk = h/6 A, and the next node
+// (rn, kn).  kMixed carries the rounding of both updates in (rl, kl)
+// (Fast2Sum); the plain form leaves them at zero.  The forward kernel and the
+// adjoint's recomputation share it, so both follow the same path.
+template <bool kMixed>
+__device__ __forceinline__ void complete_step(float h, float h2_6, float h_6, const Rk4Out& o, float px, float py,
+                                              float pz, float kx, float ky, float kz, float& rlx, float& rly,
+                                              float& rlz, float& klx, float& kly, float& klz, Vec& dr, Vec& rn,
+                                              Vec& kn) {
+  dr = {fmaf(h, kx + klx, h2_6 * o.Gx), fmaf(h, ky + kly, h2_6 * o.Gy), fmaf(h, kz + klz, h2_6 * o.Gz)};
+  const Vec dk{h_6 * o.Ax, h_6 * o.Ay, h_6 * o.Az};
+  if (kMixed) {
+    fast_two_sum(px, dr.x + rlx, rn.x, rlx);
+    fast_two_sum(py, dr.y + rly, rn.y, rly);
+    fast_two_sum(pz, dr.z + rlz, rn.z, rlz);
+    fast_two_sum(kx, dk.x + klx, kn.x, klx);
+    fast_two_sum(ky, dk.y + kly, kn.y, kly);
+    fast_two_sum(kz, dk.z + klz, kn.z, klz);
+  } else {
+    rn = {px + dr.x, py + dr.y, pz + dr.z};
+    kn = {kx + dk.x, ky + dk.y, kz + dk.z};
+  }
+}
+
+// The step-wise retrace of one central step (Eqs. 5-11): chord direction t,
+// transverse basis (e1, e2), eps, the scaled separations c1, c2 of the
+// +-e1, +-e2 pairs (2 neighbours: one-sided against the central G0), and
+// ln M.  With 8 neighbours the 45-degree pairs give a second estimate and M
+// is the mean of the two.
+struct Retrace {
+  Vec t, e1, e2, c1, c2;
+  float eps, lm;
+};
+
+template <int NB>
+__device__ __forceinline__ Retrace retrace_step(const GridDev& G, float kf, float h, float h2_6, float h2_12,
+                                                float eta, float eps_fixed, float px, float py, float pz, float kx,
+                                                float ky, float kz, const Vec& dr, const Vec& G0) {
+  Retrace R;
+  const float d2n = dot3(dr, dr);
+  const float ids = rsqrtf(d2n);
+  R.t = {dr.x * ids, dr.y * ids, dr.z * ids};  // chord direction (Eq. 5)
+  basis(R.t, R.e1, R.e2);                      // transverse basis (Eq. 6)
+  R.eps = (eps_fixed > 0.f) ? eps_fixed : eta * (d2n * ids);  // Eq. 8
+  const Vec sa{R.eps * R.e1.x, R.eps * R.e1.y, R.eps * R.e1.z}, sb{R.eps * R.e2.x, R.eps * R.e2.y, R.eps * R.e2.z};
+  // raw separations: NB >= 4: D_j = G_{+j} - G_{-j} over the +-pair j
+  // (neighbour q is the "+" (even q) or "-" (odd q) member of pair q / 2);
+  // NB == 2: D_j = G_j.  One retrace per loop trip keeps the code small.
+  constexpr int NP = (NB >= 4) ? NB / 2 : 2;
+  Vec D[NP];
+#pragma unroll
+  for (int m = 0; m < NP; ++m) D[m] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+  for (int q = 0; q < NB; ++q) {
+    const int j = (NB >= 4) ? (q >> 1) : q;
+    const float sgn = (NB >= 4 && (q & 1)) ? -1.f : 1.f;
+    const Vec off = (NB >= 4) ? pair_offset(j, sa, sb) : ((j == 0) ? sa : sb);
+    const Vec g = rk4_g3(G, kf, h, fmaf(sgn, off.x, px), fmaf(sgn, off.y, py), fmaf(sgn, off.z, pz), kx, ky, kz);
+#pragma unroll
+    for (int m = 0; m < NP; ++m)
+      if (m == j) D[m] = {fmaf(sgn, g.x, D[m].x), fmaf(sgn, g.y, D[m].y), fmaf(sgn, g.z, D[m].z)};
+  }
+  if (NB == 2) {  // one-sided: d_j = eps e_j + h^2/6 (G_j - G_0)
+    const float sc = h2_6 / R.eps;
+    R.c1 = {sc * (D[0].x - G0.x), sc * (D[0].y - G0.y), sc * (D[0].z - G0.z)};
+    R.c2 = {sc * (D[1].x - G0.x), sc * (D[1].y - G0.y), sc * (D[1].z - G0.z)};
+  } else {        // central difference: d = eps e + h^2/12 (G_+ - G_-)
+    const float sc = h2_12 / R.eps;
+    R.c1 = {sc * D[0].x, sc * D[0].y, sc * D[0].z};
+    R.c2 = {sc * D[1].x, sc * D[1].y, sc * D[1].z};
+  }
+  R.lm = ln_m(R.c1, R.c2, R.e1, R.e2, R.t);
+  if (NB == 8) {
+    const float s2 = 0.70710678118654752f, sc = h2_12 / R.eps;
+    const Vec g1{s2 * (R.e1.x + R.e2.x), s2 * (R.e1.y + R.e2.y), s2 * (R.e1.z + R.e2.z)};
+    const Vec g2{s2 * (R.e2.x - R.e1.x), s2 * (R.e2.y - R.e1.y), s2 * (R.e2.z - R.e1.z)};
+    const Vec c3{sc * D[2 % NP].x, sc * D[2 % NP].y, sc * D[2 % NP].z};
+    const Vec c4{sc * D[3 % NP].x, sc * D[3 % NP].y, sc * D[3 % NP].z};
+    const float lm2 = ln_m(c3, c4, g1, g2, R.t);
+    // M = (M_e + M_g) / 2
+    R.lm = fmaxf(R.lm, lm2) + log1p_small(__expf(-fabsf(R.lm - lm2))) - 0.69314718055994531f;
+  }
+  return R;
+}
+
 template <int NB, bool kMixed>
 __global__ void __launch_bounds__(kThreads, kRayMinBlocks) trace_rays(const __grid_constant__ TraceParams P) {
   const int lane = threadIdx.x & 31;
@@ -180,20 +266,8 @@ __global__ void __launch_bounds__(kThreads, kRayMinBlocks) trace_rays(const __gr
     }
 
     // ---------------------------------------------- (c) complete step `step`
-    const Vec dr{fmaf(h, kx + klx, P.h2_6 * o.Gx), fmaf(h, ky + kly, P.h2_6 * o.Gy), fmaf(h, kz + klz, P.h2_6 * o.Gz)};
-    const Vec dk{P.h_6 * o.Ax, P.h_6 * o.Ay, P.h_6 * o.Az};
-    Vec rn, kn;
-    if (kMixed) {
-      fast_two_sum(px, dr.x + rlx, rn.x, rlx);
-      fast_two_sum(py, dr.y + rly, rn.y, rly);
-      fast_two_sum(pz, dr.z + rlz, rn.z, rlz);
-      fast_two_sum(kx, dk.x + klx, kn.x, klx);
-      fast_two_sum(ky, dk.y + kly, kn.y, kly);
-      fast_two_sum(kz, dk.z + klz, kn.z, klz);
-    } else {
-      rn = {px + dr.x, py + dr.y, pz + dr.z};
-      kn = {kx + dk.x, ky + dk.y, kz + dk.z};
-    }
+    Vec dr, rn, kn;
+    complete_step<kMixed>(h, P.h2_6, P.h_6, o, px, py, pz, kx, ky, kz, rlx, rly, rlz, klx, kly, klz, dr, rn, kn);
     kap_prev = kap;
     te_prev = o.te1;
     const float rr2 = dot3(rn, rn);
@@ -204,54 +278,9 @@ __global__ void __launch_bounds__(kThreads, kRayMinBlocks) trace_rays(const __gr
 
     // ---------------------------------------------- (d) neighbour retrace of step `step`
     if (NB > 0 && term != kNan) {
-      const float d2n = dot3(dr, dr);
-      const float ids = rsqrtf(d2n);
-      const Vec tp{dr.x * ids, dr.y * ids, dr.z * ids};  // chord direction (Eq. 5)
-      Vec e1, e2;
-      basis(tp, e1, e2);                                 // transverse basis (Eq. 6)
-      const float eps = (P.eps_fixed > 0.f) ? P.eps_fixed : P.eta * (d2n * ids);  // Eq. 8
-      const Vec sa{eps * e1.x, eps * e1.y, eps * e1.z}, sb{eps * e2.x, eps * e2.y, eps * e2.z};
-      // raw separations: NB >= 4: D_j = G_{+j} - G_{-j} over the +-pair j; NB == 2: G_j
-      constexpr int NP = (NB >= 4) ? NB / 2 : 2;
-      Vec D[NP];
-#pragma unroll 1
-      for (int j = 0; j < NP; ++j) {
-        Vec g;
-        if (NB >= 4) {
-          const Vec off = pair_offset(j, sa, sb);
-          const Vec gp = rk4_g3(P.G, kf, h, px + off.x, py + off.y, pz + off.z, kx, ky, kz);
-          const Vec gm = rk4_g3(P.G, kf, h, px - off.x, py - off.y, pz - off.z, kx, ky, kz);
-          g = {gp.x - gm.x, gp.y - gm.y, gp.z - gm.z};
-        } else {
-          const Vec off = (j == 0) ? sa : sb;
-          g = rk4_g3(P.G, kf, h, px + off.x, py + off.y, pz + off.z, kx, ky, kz);
-        }
-#pragma unroll
-        for (int m = 0; m < NP; ++m)
-          if (m == j) D[m] = g;
-      }
-      Vec c1, c2;
-      if (NB == 2) {  // one-sided: d_j = eps e_j + h^2/6 (G_j - G_0)
-        const float sc = P.h2_6 / eps;
-        c1 = {sc * (D[0].x - o.Gx), sc * (D[0].y - o.Gy), sc * (D[0].z - o.Gz)};
-        c2 = {sc * (D[1].x - o.Gx), sc * (D[1].y - o.Gy), sc * (D[1].z - o.Gz)};
-      } else {        // central difference: d = eps e + h^2/12 (G_+ - G_-)
-        const float sc = P.h2_12 / eps;
-        c1 = {sc * D[0].x, sc * D[0].y, sc * D[0].z};
-        c2 = {sc * D[1].x, sc * D[1].y, sc * D[1].z};
-      }
-      float lm = ln_m(c1, c2, e1, e2, tp);
-      if (NB == 8) {
-        const float s2 = 0.70710678118654752f, sc = P.h2_12 / eps;
-        const Vec g1{s2 * (e1.x + e2.x), s2 * (e1.y + e2.y), s2 * (e1.z + e2.z)};
-        const Vec g2{s2 * (e2.x - e1.x), s2 * (e2.y - e1.y), s2 * (e2.z - e1.z)};
-        const Vec c3{sc * D[2 % NP].x, sc * D[2 % NP].y, sc * D[2 % NP].z};
-        const Vec c4{sc * D[3 % NP].x, sc * D[3 % NP].y, sc * D[3 % NP].z};
-        const float lm2 = ln_m(c3, c4, g1, g2, tp);
-        // M = (M_e + M_g) / 2
-        lm = fmaxf(lm, lm2) + log1p_small(__expf(-fabsf(lm - lm2))) - 0.69314718055994531f;
-      }
-      acc_add<kMixed>(lns_hi, lns_lo, lm);
+      const Retrace R = retrace_step<NB>(P.G, kf, h, P.h2_6, P.h2_12, P.eta, P.eps_fixed, px, py, pz, kx, ky, kz,
+                                         dr, Vec{o.Gx, o.Gy, o.Gz});
+      acc_add<kMixed>(lns_hi, lns_lo, R.lm);
     }
 
     // ---------------------------------------------- (e) next node, or the end of the path

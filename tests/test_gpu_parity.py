@@ -11,19 +11,27 @@ stage points fall within rounding distance of a cell face (the
 interpolant's gradient jumps there), so on a corona that is rough at the
 cell scale no FP32 implementation reproduces every FP64 ray.  The oracle
 measures each ray's own sensitivity by re-tracing it with every lookup's r
-perturbed by a relative 1e-7 and theta, phi by 3e-7 rad (the size of the
-GPU's FP32 geometry rounding; eight seeds, since a face flip is a rare event
-per stage point).  A ray is well-conditioned when no seed flips its status
-and the largest change stays below a tenth of each bar (T_b, and the exit
-and ln S where they are checked).  Every well-conditioned ray is held to the
-strict bars.  An ill-conditioned ray is held to max(strict bar, 10 x its
-spread) in T_b, capped at 1e-2 of the scale (TB_CAP), and its status only if
-the status did not flip under the probe; its exit point and ln S are
-reported, not bounded (on chaotic rays they differ by up to whole R_sun
-between two correct FP32 runs).  Each test states the fraction of its rays
-that must be well-conditioned (the bound is not vacuous) and prints, per
-frequency, the fraction that is, the largest T_b bound granted and the
-largest exit difference among the ill-conditioned rays.
+perturbed by a relative JITTER and theta, phi by 3 JITTER rad.  JITTER =
+1e-6 is ten times the GPU's FP32 geometry rounding: a face flip is a rare
+event per stage point, and a probe at the rounding amplitude itself (1e-7,
+eight seeds) missed rays that the GPU's own rounding did flip (the GPU then
+missed the strict bars by 600 times the probe's spread), so the
+classification uses the stronger probe.  A ray is well-conditioned when no
+seed flips its status and its largest change stays below a tenth of the
+bar, for each output separately: T_b; the exit point of a ray ending on a
+sphere; ln S where a test checks it.  A ray is held to the strict bar of
+every output it is well-conditioned for.  In T_b an ill-conditioned ray is
+held to TB_CAP = 1e-2 of the scale; its exit point and ln S are reported,
+not bounded (on chaotic rays they differ by up to whole R_sun between two
+correct FP32 runs).  Status must match unless it flipped under the probe.
+Each test states the fraction of its rays that must be T_b-well-conditioned
+(so that the strict bar is not vacuous), measured with the oracle alone:
+the step-wise tests on smooth coronae ~100% (floor 90%), the white-noise
+corona 87% (floor 80%), tube mode 50-63% (floor 40%: persistent neighbours
+carry every face kink to the end of the path), the headline corona's
+sampled rays 74% (4% at 40 MHz rising to 100% from 241 MHz; floor 65%).
+Each comparison prints, per frequency, the well-conditioned fractions of
+each output and the largest errors among well- and ill-conditioned rays.
 """
 import numpy as np
 import pytest
@@ -35,8 +43,8 @@ pytestmark = pytest.mark.gpu
 TB_REL = 1e-3
 EXIT_ABS = 1e-4
 TB_CAP = 1e-2
-JITTER = 1e-7
-SEEDS = 8
+JITTER = 1e-6
+SEEDS = 6
 
 
 @pytest.fixture(scope="module")
@@ -105,10 +113,31 @@ def _scale(ref_tb):
     return np.maximum(ref_tb, np.maximum(1e-2 * ref_tb.max(axis=1, keepdims=True), 1e-30))
 
 
+def classify(ref, cond, tb_rel=TB_REL, exit_abs=EXIT_ABS, lns_abs=None):
+    """Per-output conditioning of each ray (see the module docstring):
+    (well_tb, well_exit, well_lns, flip).  A ray is well-conditioned for an
+    output when no probe seed flips its status and the probe moves that
+    output by less than a tenth of its bar."""
+    scale = _scale(ref["tb"])
+    ends = (ref["status"] == 1) | (ref["status"] == 2)
+    if cond is None:
+        ok = np.ones(ref["tb"].shape, bool)
+        return ok, ok & ends, ok, ~ok
+    stb, sex, sls, flip = cond
+    well_tb = ~flip & (stb <= 0.1 * tb_rel * scale)
+    well_ex = ~flip & ends & (sex <= 0.1 * exit_abs)
+    well_ls = ~flip & (sls <= 0.1 * max(lns_abs if lns_abs is not None else 0.0, 1e-30))
+    return well_tb, well_ex, well_ls, flip
+
+
 def compare(gpu, ref, pixels=None, tb_rel=TB_REL, exit_abs=EXIT_ABS, lns_abs=None, cond=None, label="",
             min_well=0.6, freqs=None):
-    """Element-by-element comparison (see the module docstring for the bars);
-    returns a report with the per-frequency fraction of well-conditioned rays."""
+    """Element-by-element comparison (see the module docstring for the bars):
+    T_b of T_b-well-conditioned rays within tb_rel of the scale, of the others
+    within TB_CAP; exit points of exit-well-conditioned rays within exit_abs;
+    ln S of ln S-well-conditioned rays within lns_abs.  At least min_well of
+    the rays must be T_b-well-conditioned.  Returns a report with the
+    per-frequency fractions and largest errors."""
     sel = (lambda a: a) if pixels is None else (lambda a: a[:, pixels])
     g_tb, g_st, g_ex, g_ls = sel(gpu["tb"]), sel(gpu["status"]), sel(gpu["exit"]), sel(gpu["ln_s"])
     scale = _scale(ref["tb"])
@@ -116,17 +145,8 @@ def compare(gpu, ref, pixels=None, tb_rel=TB_REL, exit_abs=EXIT_ABS, lns_abs=Non
     dex = np.linalg.norm(g_ex - ref["exit"], axis=-1)
     dls = np.abs(g_ls - ref["ln_s"])
     ends = (ref["status"] == 1) | (ref["status"] == 2)
-    if cond is None:
-        well = np.ones(ref["tb"].shape, bool)
-        flip = np.zeros(ref["tb"].shape, bool)
-        tb_bound = tb_rel * scale
-    else:
-        stb, sex, sls, flip = cond
-        well = ~flip & (stb <= 0.1 * tb_rel * scale) & (~ends | (sex <= 0.1 * exit_abs))
-        if lns_abs is not None:
-            well &= sls <= 0.1 * max(lns_abs, 1e-30)
-        tb_bound = np.where(well, tb_rel * scale,
-                            np.minimum(np.maximum(tb_rel * scale, 10 * stb), TB_CAP * scale))
+    well, well_ex, well_ls, flip = classify(ref, cond, tb_rel, exit_abs, lns_abs)
+    tb_bound = np.where(well, tb_rel * scale, TB_CAP * scale)
     bad_st = ~flip & (g_st != ref["status"])
     assert not bad_st.any(), f"{label}: status differs at {np.argwhere(bad_st)[:5]}"
     bad_tb = dtb > tb_bound
@@ -135,37 +155,39 @@ def compare(gpu, ref, pixels=None, tb_rel=TB_REL, exit_abs=EXIT_ABS, lns_abs=Non
         det = [(i, g_tb[i], ref["tb"][i], tb_bound[i], bool(well[i]), cond[0][i] if cond else None) for i in idx]
         raise AssertionError(f"{label}: T_b out of bounds (idx, gpu, oracle, bound, well, spread) {det}; "
                              f"max rel {(dtb / scale).max():.3e}")
-    chk = ends & well
-    bad_ex = chk & (dex > exit_abs)
+    bad_ex = well_ex & (dex > exit_abs)
     if bad_ex.any():
         idx = [tuple(i) for i in np.argwhere(bad_ex)[:4]]
         det = [(i, dex[i], cond[1][i] if cond else None, ref["status"][i]) for i in idx]
-        raise AssertionError(f"{label}: exit error of well-conditioned rays (idx, err, spread, status) {det}")
+        raise AssertionError(f"{label}: exit error of exit-well-conditioned rays (idx, err, spread, status) {det}")
     if lns_abs is not None:
-        bad_ls = well & (dls > lns_abs)
+        bad_ls = well_ls & (dls > lns_abs)
         if bad_ls.any():
             idx = [tuple(i) for i in np.argwhere(bad_ls)[:4]]
-            det = [(i, g_ls[i], ref["ln_s"][i]) for i in idx]
-            raise AssertionError(f"{label}: ln S of well-conditioned rays out of bounds (idx, gpu, oracle) {det}")
-    frac = float(well.mean())
+            det = [(i, g_ls[i], ref["ln_s"][i], cond[2][i] if cond else None) for i in idx]
+            raise AssertionError(f"{label}: ln S of ln S-well-conditioned rays out of bounds (idx, gpu, oracle, "
+                                 f"spread) {det}")
+    rel = dtb / scale
+
+    def mx(a, m):
+        return float(a[m].max()) if m.any() else 0.0
     per_f = []
     for fi in range(ref["tb"].shape[0]):
-        ill = ~well[fi]
         per_f.append({"f_MHz": None if freqs is None else round(float(freqs[fi]) / 1e6, 2),
-                      "well": round(float(well[fi].mean()), 4),
-                      "max_tb_rel_well": float((dtb[fi] / scale[fi])[well[fi]].max()) if well[fi].any() else 0.0,
-                      "max_tb_bound_rel": float((tb_bound[fi] / scale[fi]).max()),
-                      "max_exit_well": float(dex[fi][well[fi] & ends[fi]].max()) if (well[fi] & ends[fi]).any()
-                      else 0.0,
-                      "max_exit_ill": float(dex[fi][ill & ends[fi]].max()) if (ill & ends[fi]).any() else 0.0})
-    report = {"label": label, "rays": int(well.size), "well": round(frac, 4),
-              "max_tb_rel": float((dtb / scale).max()),
-              "max_tb_rel_well": float((dtb / scale)[well].max()) if well.any() else 0.0,
-              "max_exit_well": float(dex[chk].max()) if chk.any() else 0.0,
-              "max_lns_well": float(dls[well].max()) if well.any() else 0.0,
+                      "well_tb": round(float(well[fi].mean()), 4),
+                      "well_exit": round(float(well_ex[fi].sum() / max(ends[fi].sum(), 1)), 4),
+                      "well_lns": round(float(well_ls[fi].mean()), 4) if lns_abs is not None else None,
+                      "max_tb_rel_well": mx(rel[fi], well[fi]), "max_tb_rel_ill": mx(rel[fi], ~well[fi]),
+                      "max_exit_well": mx(dex[fi], well_ex[fi]), "max_exit_ill": mx(dex[fi], ends[fi] & ~well_ex[fi])})
+    report = {"label": label, "rays": int(well.size), "well_tb": round(float(well.mean()), 4),
+              "well_exit": round(float(well_ex.sum() / max(ends.sum(), 1)), 4),
+              "well_lns": round(float(well_ls.mean()), 4) if lns_abs is not None else None,
+              "max_tb_rel": float(rel.max()), "max_tb_rel_well": mx(rel, well),
+              "max_exit_well": mx(dex, well_ex), "max_lns_well": mx(dls, well_ls) if lns_abs is not None else None,
               "per_frequency": per_f}
     print("parity", report)
-    assert frac >= min_well, f"{label}: only {frac:.1%} of rays well-conditioned (need {min_well:.0%})"
+    frac = float(well.mean())
+    assert frac >= min_well, f"{label}: only {frac:.1%} of rays T_b-well-conditioned (need {min_well:.0%})"
     return report
 
 
@@ -256,7 +278,7 @@ def test_neighbour_counts_and_modes(rt, ctx, orc, n_nb, s_mode):
     ref = run_oracle(orc, g, v, freqs, n_nb=n_nb, s_mode=s_mode)
     cond = spreads(orc, g, v, freqs, ref, n_nb=n_nb, s_mode=s_mode)
     compare(gpu, ref, cond=cond, lns_abs=0.0 if s_mode == 2 else 1e-3, label=f"nb{n_nb} mode{s_mode}",
-            min_well=TUBE_MIN_WELL if s_mode == 1 else 0.6)
+            min_well=TUBE_MIN_WELL if s_mode == 1 else 0.9)
 
 
 # Tube mode (persistent neighbours) on the trilinear interpolant is far less
@@ -264,11 +286,10 @@ def test_neighbour_counts_and_modes(rt, ctx, orc, n_nb, s_mode):
 # that crosses a cell face one step earlier or later than in the reference
 # changes its acceleration by the face's kink, a jump as large as the whole
 # offset difference, and the tube carries it to the end of the path.
-# Measured with the oracle's own 1e-6 perturbation on this view, 35-63% of
-# the tube rays (any of 64 to 1024 radial nodes) against 100% of the
-# step-wise rays stay within a tenth of the T_b bar; the per-ray bounds stay,
-# the non-vacuity floor for tube mode is 30%.
-TUBE_MIN_WELL = 0.3
+# Measured with the oracle's own 1e-6 probe, 50-63% of the tube rays of
+# these views are T_b-well-conditioned (and only 23-39% in ln S) against
+# ~100% of the step-wise rays; the floor for tube mode is 40%.
+TUBE_MIN_WELL = 0.4
 
 
 @pytest.mark.parametrize("n_nb", [2, 4, 8])
@@ -297,7 +318,7 @@ def test_rough_corona_conditioned(rt, ctx, orc, tiny):
     grid = ctx.load(gm)
     gpu = run_gpu(rt, ctx, grid, v, freqs, precision=1)
     ref = run_oracle(orc, gm, v, freqs)
-    compare(gpu, ref, cond=spreads(orc, gm, v, freqs, ref), label="rough")
+    compare(gpu, ref, cond=spreads(orc, gm, v, freqs, ref), label="rough", min_well=0.8)
 
 
 def test_straight_line_of_sight(rt, ctx, orc, tiny):
@@ -416,4 +437,4 @@ def test_global_corona_sampled(rt, ctx, orc):
 
 
 GLOBAL_LNS_ABS = 1e-3
-GLOBAL_MIN_WELL = 0.6
+GLOBAL_MIN_WELL = 0.65

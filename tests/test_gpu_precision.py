@@ -3,8 +3,15 @@ frequencies 40-800 MHz, 8 neighbours, traced in full in both arithmetic
 forms; per-output error against the FP64 oracle on a sampled pixel set
 (every 64th pixel in x and y, 8 of the 32 frequencies).
 
-The compensated form must meet the strict bar (the corona is spherically
-symmetric, hence well-conditioned); the plain FP32 form is reported.
+The compensated form must meet the strict T_b and exit bars (the corona is
+spherically symmetric, hence well-conditioned); the plain FP32 form is
+reported.  ln S and tau: the oracle itself, re-traced with every lookup's
+r perturbed by a relative 1e-7 and theta, phi by 3e-7 rad (the GPU's FP32
+geometry rounding), moves the tau of these rays by up to 1.03e-4 (relative)
+and their ln S by up to 1.59e-4 (99th percentiles 8.6e-6 and 8.9e-6): that
+is the conditioning floor of the worst rays (deep, near-grazing rays), not
+arithmetic.  So the bars are 3e-4 on the worst ray (twice that floor) and
+1e-4 on the 99th percentile.
 """
 import json
 
@@ -42,11 +49,15 @@ def test_precision_at_scale(orc):
         gst = dd["status"].reshape(len(f), -1)[fsel][:, pix]
         scale = np.maximum(ref["tb"], 1e-2 * ref["tb"].max(axis=1, keepdims=True))
         ends = (ref["status"] == 1) | (ref["status"] == 2)
+        dls = np.abs(gls - ref["ln_s"])
+        dtau = np.abs(gtau - ref["tau"]) / np.maximum(ref["tau"], 1e-3)
         report[name] = {
             "tb_rel_max": float((np.abs(gtb - ref["tb"]) / scale).max()),
             "exit_max_rsun": float(np.linalg.norm(gex - ref["exit"], axis=-1)[ends].max()),
-            "ln_s_abs_max": float(np.abs(gls - ref["ln_s"]).max()),
-            "tau_rel_max": float((np.abs(gtau - ref["tau"]) / np.maximum(ref["tau"], 1e-3)).max()),
+            "ln_s_abs_max": float(dls.max()),
+            "ln_s_abs_p99": float(np.percentile(dls, 99)),
+            "tau_rel_max": float(dtau.max()),
+            "tau_rel_p99": float(np.percentile(dtau, 99)),
             "status_mismatch": int((gst != ref["status"]).sum()),
             "rays_compared": int(ref["tb"].size),
         }
@@ -55,4 +66,5 @@ def test_precision_at_scale(orc):
     assert m["status_mismatch"] == 0
     assert m["tb_rel_max"] <= 1e-3
     assert m["exit_max_rsun"] <= 1e-4
-    assert m["ln_s_abs_max"] <= 1e-3
+    assert m["ln_s_abs_max"] <= 3e-4 and m["ln_s_abs_p99"] <= 1e-4
+    assert m["tau_rel_max"] <= 3e-4 and m["tau_rel_p99"] <= 1e-4
