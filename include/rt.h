@@ -299,6 +299,50 @@ rt_status rt_trace_batch_noalloc(const rt_grid* grid, const rt_request* reqs, in
 rt_status rt_disk_mean_tb(const rt_view* view, const float* tb, int nf, double radius, double* mean_out,
                           void* stream);
 
+/* One node of a recorded ray path (32 bytes). */
+typedef struct {
+  float r[3];     /* position [R_sun]                                                  */
+  float ln_s;     /* ln(S / S_0) at the node                                           */
+  float dlns_ds;  /* ln M of the step arriving at the node / its chord length [1/R_sun] */
+  float tau;      /* optical depth from the entry to the node                          */
+  float ne, te;   /* interpolated n_e [cm^-3] and T_e [K] at the node                  */
+} rt_path_node;
+
+/* Ray-fan diagnostics (Sec. 3.2, Figs. 4 and 6): the whole path of the rays
+ * of selected pixels at one frequency, node by node (entry node first; the
+ * crossing point last on a ray that ends on a sphere), with the local
+ * magnification rate d ln S/ds = ln M / ds of each step.  The rays are
+ * stepped with the same code and in the same order as rt_trace_image, so
+ * their T_b and diagnostics equal its values for those pixels.
+ * pixels:  host [n], flat indices iy * nx + ix of `view` (1 <= n <= 2^20).
+ * opt:     step-wise magnification or none (tube mode: RT_ERR_UNSUPPORTED).
+ * nodes:   device [n][cap] rt_path_node, caller-owned: ray i's first cap
+ *          nodes (a longer path is cut, its n_nodes still counts them all).
+ * n_nodes: device [n] int, the node count of each path.
+ * tb_out:  device [n] float, the rays' T_b.
+ * diag:    device [n] rt_ray_diag, or NULL.
+ * Asynchronous on `stream` (a small stream-ordered allocation holds the
+ * pixel list).  Errors: RT_ERR_ARG, RT_ERR_UNSUPPORTED, RT_ERR_CUDA. */
+rt_status rt_trace_paths(rt_ctx* ctx, const rt_grid* grid, const rt_view* view, double freq_hz, const int* pixels,
+                         int n, const rt_options* opt, int cap, rt_path_node* nodes, int* n_nodes, float* tb_out,
+                         rt_ray_diag* diag, void* stream);
+
+/* Beam-convolved maps (Sec. 3.3, Figs. 7-8: the maps as an interferometer
+ * of maximum baseline B would see them).  Each map f is convolved with a
+ * circular Gaussian beam of FWHM lambda_f / B radians, placed on the image
+ * plane at 1 AU (FWHM in R_sun = lambda_f / B x 215.03), separably (rows,
+ * then columns) with zero outside the image.  The weights are the samples of
+ * exp(-d^2 / 2 sigma^2) at the integer pixel offsets |d| <= ceil(4 sigma),
+ * normalised to sum to 1 per pass.  Sums in FP64.
+ * view:      host; the view the maps were traced with (square pixels).
+ * tb:        device [nf][ny][nx] float.
+ * freqs_hz:  host [nf], > 0 (1 <= nf <= 64); baseline_m > 0.
+ * scratch:   device [nf][ny][nx] float, caller-owned work space.
+ * tb_out:    device [nf][ny][nx] float, caller-owned (may not alias tb or scratch).
+ * Asynchronous on `stream`.  Errors: RT_ERR_ARG, RT_ERR_CUDA. */
+rt_status rt_beam_convolve(const rt_view* view, const float* tb, const double* freqs_hz, int nf, double baseline_m,
+                           float* scratch, float* tb_out, void* stream);
+
 /* Samples the interpolated corona at n points: the field evaluation of
  * every RK4 stage (trilinear n_e, T_e in (r, theta, phi) and the exact
  * Cartesian gradient of the n_e interpolant; Sec. 3.1-3.2, Eq. 4).

@@ -9,6 +9,7 @@ no code with the CUDA library; the two meet only in the seeded inputs of
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -281,4 +282,35 @@ def disk_mean_tb(view, tb, radius=0.5):
     if not inside.any():
         return np.zeros(tb.shape[0])
     return np.array([m[inside].mean() for m in tb])
+
+
+C_CM_S = 2.99792458e10               # speed of light [cm/s]
+AU_RSUN = 1.495978707e13 / 6.957e10  # 1 AU in R_sun (IAU)
+
+
+def beam_sigma_pixels(view, f_hz, baseline_m):
+    """Standard deviation, in pixels of ``view``, of the circular Gaussian beam
+    of an interferometer of maximum baseline B (Sec. 3.3): FWHM = lambda / B
+    radians, placed on the image plane at 1 AU."""
+    fwhm_rsun = C_CM_S / f_hz / (baseline_m * 100.0) * AU_RSUN
+    dx = abs(view.x1 - view.x0) / view.nx
+    return fwhm_rsun / math.sqrt(8.0 * math.log(2.0)) / dx
+
+
+def beam_convolve(view, tb, freqs, baseline_m):
+    """The maps tb [nf, ny, nx] convolved with the beam of beam_sigma_pixels:
+    separable, rows then columns, zero outside the image, with the samples
+    exp(-d^2 / 2 sigma^2) at |d| <= ceil(4 sigma) normalised to sum 1."""
+    from scipy.ndimage import convolve1d
+    tb = np.asarray(tb, dtype=np.float64).reshape(-1, view.ny, view.nx)
+    out = np.empty_like(tb)
+    for i, f in enumerate(np.atleast_1d(freqs)):
+        sigma = beam_sigma_pixels(view, float(f), baseline_m)
+        hw = int(math.ceil(4.0 * sigma))
+        d = np.arange(-hw, hw + 1, dtype=np.float64)
+        w = np.exp(-0.5 * d * d / (sigma * sigma))
+        w /= w.sum()
+        rows = convolve1d(tb[i], w, axis=1, mode="constant", cval=0.0)
+        out[i] = convolve1d(rows, w, axis=0, mode="constant", cval=0.0)
+    return out
 

@@ -250,6 +250,54 @@ class Context:
                                     C.c_void_p(out.data_ptr()), _stream_ptr(stream)), "rt_disk_mean_tb")
         return out
 
+    def trace_paths(self, grid: Grid, v, freq_hz, pixels, opts=None, cap=100000, stream=None):
+        """rt_trace_paths: the node-by-node paths of the rays of `pixels` (flat
+        indices of view v) at one frequency.  Returns a list of dicts of numpy
+        arrays (r [m, 3], ln_s, dlns_ds, tau, ne, te) and the rays' T_b and
+        diagnostics."""
+        import torch
+        vs = view(v)
+        pix = np.ascontiguousarray(np.atleast_1d(pixels), dtype=np.int32)
+        n = len(pix)
+        dev = torch.device("cuda", self.device)
+        nodes = torch.empty((n, cap, 8), dtype=torch.float32, device=dev)
+        counts = torch.empty(n, dtype=torch.int32, device=dev)
+        tb = torch.empty(n, dtype=torch.float32, device=dev)
+        d = torch.empty((n, 7), dtype=torch.int32, device=dev)
+        o = opts if opts is not None else options()
+        check(lib().rt_trace_paths(self.handle, grid.handle, C.byref(vs), float(freq_hz),
+                                   pix.ctypes.data_as(C.POINTER(C.c_int)), n, C.byref(o), int(cap),
+                                   C.c_void_p(nodes.data_ptr()), C.c_void_p(counts.data_ptr()),
+                                   C.c_void_p(tb.data_ptr()), C.c_void_p(d.data_ptr()), _stream_ptr(stream)),
+              "rt_trace_paths")
+        torch.cuda.synchronize(dev)
+        nd, cn = nodes.cpu().numpy(), counts.cpu().numpy()
+        paths = []
+        for i in range(n):
+            m = min(int(cn[i]), cap)
+            a = nd[i, :m]
+            paths.append({"r": a[:, 0:3].astype(np.float64), "ln_s": a[:, 3].astype(np.float64),
+                          "dlns_ds": a[:, 4].astype(np.float64), "tau": a[:, 5].astype(np.float64),
+                          "ne": a[:, 6].astype(np.float64), "te": a[:, 7].astype(np.float64),
+                          "n_nodes": int(cn[i])})
+        return paths, tb, d
+
+    def beam_convolve(self, v, tb, freqs, baseline_m, stream=None):
+        """rt_beam_convolve: the maps tb ([nf, ny, nx] float32 CUDA tensor traced
+        with view v at freqs) convolved with the Gaussian beam of an
+        interferometer of maximum baseline baseline_m metres."""
+        import torch
+        vs = view(v)
+        f = np.ascontiguousarray(np.atleast_1d(freqs), dtype=np.float64)
+        assert tb.is_cuda and tb.dtype == torch.float32 and tb.is_contiguous()
+        assert tb.numel() == len(f) * vs.nx * vs.ny
+        scratch = torch.empty_like(tb)
+        out = torch.empty_like(tb)
+        check(lib().rt_beam_convolve(C.byref(vs), C.c_void_p(tb.data_ptr()), f.ctypes.data_as(C.POINTER(C.c_double)),
+                                     len(f), float(baseline_m), C.c_void_p(scratch.data_ptr()),
+                                     C.c_void_p(out.data_ptr()), _stream_ptr(stream)), "rt_beam_convolve")
+        return out
+
     def probe_field(self, grid: Grid, xyz, stream=None):
         """rt_probe_field: (n_e, T_e, grad n_e) at points xyz [n, 3] -> [n, 5]."""
         import torch

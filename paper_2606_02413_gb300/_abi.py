@@ -25,7 +25,7 @@ EXPORTS = ["rt_default_options", "rt_status_string", "rt_last_error", "rt_create
            "rt_load_grid", "rt_free_grid", "rt_trace_image", "rt_backward", "rt_batch_plan_create",
            "rt_batch_plan_create_shard", "rt_shard_assign", "rt_batch_plan_launch",
            "rt_batch_plan_stats", "rt_batch_plan_destroy", "rt_trace_batch", "rt_trace_batch_noalloc",
-           "rt_probe_field", "rt_disk_mean_tb", "rt_sync", "rt_get_stats"]
+           "rt_probe_field", "rt_disk_mean_tb", "rt_beam_convolve", "rt_trace_paths", "rt_sync", "rt_get_stats"]
 
 
 class GridDesc(C.Structure):
@@ -106,13 +106,16 @@ def lib():
         L.rt_trace_batch.argtypes = [vp, vp, C.POINTER(Request), ip, C.POINTER(Options), vp]
         L.rt_trace_batch_noalloc.argtypes = [vp, C.POINTER(Request), ip, C.POINTER(Options), vp]
         L.rt_disk_mean_tb.argtypes = [C.POINTER(View), vp, ip, C.c_double, vp, vp]
+        L.rt_beam_convolve.argtypes = [C.POINTER(View), vp, C.POINTER(C.c_double), ip, C.c_double, vp, vp, vp]
+        L.rt_trace_paths.argtypes = [vp, vp, C.POINTER(View), C.c_double, C.POINTER(C.c_int), ip, C.POINTER(Options),
+                                     ip, vp, vp, vp, vp, vp]
         L.rt_sync.argtypes = [vp, vp]
         L.rt_get_stats.argtypes = [vp, vp, C.POINTER(Stats)]
         for name in ("rt_create", "rt_destroy", "rt_load_grid", "rt_free_grid", "rt_trace_image", "rt_backward",
                      "rt_batch_plan_create", "rt_batch_plan_create_shard", "rt_shard_assign",
                      "rt_batch_plan_launch", "rt_batch_plan_stats",
                      "rt_batch_plan_destroy", "rt_trace_batch", "rt_trace_batch_noalloc", "rt_probe_field",
-                     "rt_disk_mean_tb", "rt_sync", "rt_get_stats"):
+                     "rt_disk_mean_tb", "rt_beam_convolve", "rt_trace_paths", "rt_sync", "rt_get_stats"):
             getattr(L, name).restype = ip
         _lib = L
         return _lib

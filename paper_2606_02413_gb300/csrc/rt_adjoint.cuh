@@ -188,77 +188,58 @@ __device__ __forceinline__ Vec force_adjoint(const GridDev& G, float kf, float x
   return {kf * gx.d, kf * gy.d, kf * gz.d};
 }
 
-// Reverse of one RK4 step from (p, k) (see rk4_step), given the adjoints of
-// its outputs: lr = dL/dr', lk = dL/dk', and extra adjoints lg on
-// G = a1 + a2 + a3 (the neighbours' separations enter only through G).
-// Accumulates dL/dp and dL/dk into lp, lk_out and scatters the n_e nodes.
-__device__ __forceinline__ void rk4_reverse(const GridDev& G, float kf, float h, const Vec& p, const Vec& k,
-                                            const Vec& lr, const Vec& lk, const Vec& lg, Vec& lp, Vec& lk_out,
-                                            float* dne) {
-  const float hh = 0.5f * h;
-  // forward stages
-  const Sample s1 = eval_field(G, p.x, p.y, p.z, false);
-  const Vec a1{kf * s1.gx, kf * s1.gy, kf * s1.gz};
-  const Vec p2{fmaf(hh, k.x, p.x), fmaf(hh, k.y, p.y), fmaf(hh, k.z, p.z)};
-  const Vec k2{fmaf(hh, a1.x, k.x), fmaf(hh, a1.y, k.y), fmaf(hh, a1.z, k.z)};
-  const Sample s2 = eval_field(G, p2.x, p2.y, p2.z, false);
-  const Vec a2{kf * s2.gx, kf * s2.gy, kf * s2.gz};
-  const Vec p3{fmaf(hh, k2.x, p.x), fmaf(hh, k2.y, p.y), fmaf(hh, k2.z, p.z)};
-  const Vec k3{fmaf(hh, a2.x, k.x), fmaf(hh, a2.y, k.y), fmaf(hh, a2.z, k.z)};
-  const Vec p4{fmaf(h, k3.x, p.x), fmaf(h, k3.y, p.y), fmaf(h, k3.z, p.z)};
-  // output adjoints: r' = r + h/6 (k + 2k2 + 2k3 + k4), k' = k + h/6 (a1 + 2a2 + 2a3 + a4)
-  const float h6 = h / 6.f, h3 = h / 3.f;
-  Vec Lp = lr;
-  Vec Lk{lk.x + h6 * lr.x, lk.y + h6 * lr.y, lk.z + h6 * lr.z};
-  Vec Lk2{h3 * lr.x, h3 * lr.y, h3 * lr.z};
-  Vec Lk3 = Lk2;
-  const Vec Lk4{h6 * lr.x, h6 * lr.y, h6 * lr.z};
-  Vec La1{h6 * lk.x + lg.x, h6 * lk.y + lg.y, h6 * lk.z + lg.z};
-  Vec La2{h3 * lk.x + lg.x, h3 * lk.y + lg.y, h3 * lk.z + lg.z};
-  Vec La3{h3 * lk.x + lg.x, h3 * lk.y + lg.y, h3 * lk.z + lg.z};
-  const Vec La4{h6 * lk.x, h6 * lk.y, h6 * lk.z};
-  // stage 4: a4 = A(p4), p4 = p + h k3, k4 = k + h a3
-  Vec Lp4 = force_adjoint(G, kf, p4.x, p4.y, p4.z, La4, dne);
-  Lp = {Lp.x + Lp4.x, Lp.y + Lp4.y, Lp.z + Lp4.z};
-  Lk3 = {fmaf(h, Lp4.x, Lk3.x), fmaf(h, Lp4.y, Lk3.y), fmaf(h, Lp4.z, Lk3.z)};
-  Lk = {Lk.x + Lk4.x, Lk.y + Lk4.y, Lk.z + Lk4.z};
-  La3 = {fmaf(h, Lk4.x, La3.x), fmaf(h, Lk4.y, La3.y), fmaf(h, Lk4.z, La3.z)};
-  // stage 3: a3 = A(p3), p3 = p + hh k2, k3 = k + hh a2
-  const Vec Lp3 = force_adjoint(G, kf, p3.x, p3.y, p3.z, La3, dne);
-  Lp = {Lp.x + Lp3.x, Lp.y + Lp3.y, Lp.z + Lp3.z};
-  Lk2 = {fmaf(hh, Lp3.x, Lk2.x), fmaf(hh, Lp3.y, Lk2.y), fmaf(hh, Lp3.z, Lk2.z)};
-  Lk = {Lk.x + Lk3.x, Lk.y + Lk3.y, Lk.z + Lk3.z};
-  La2 = {fmaf(hh, Lk3.x, La2.x), fmaf(hh, Lk3.y, La2.y), fmaf(hh, Lk3.z, La2.z)};
-  // stage 2: a2 = A(p2), p2 = p + hh k, k2 = k + hh a1
-  const Vec Lp2 = force_adjoint(G, kf, p2.x, p2.y, p2.z, La2, dne);
-  Lp = {Lp.x + Lp2.x, Lp.y + Lp2.y, Lp.z + Lp2.z};
-  Lk = {fmaf(hh, Lp2.x, Lk.x + Lk2.x), fmaf(hh, Lp2.y, Lk.y + Lk2.y), fmaf(hh, Lp2.z, Lk.z + Lk2.z)};
-  La1 = {fmaf(hh, Lk2.x, La1.x), fmaf(hh, Lk2.y, La1.y), fmaf(hh, Lk2.z, La1.z)};
-  // stage 1: a1 = A(p)
-  const Vec Lp1 = force_adjoint(G, kf, p.x, p.y, p.z, La1, dne);
-  lp = {lp.x + Lp.x + Lp1.x, lp.y + Lp.y + Lp1.y, lp.z + Lp.z + Lp1.z};
-  lk_out = {lk_out.x + Lk.x, lk_out.y + Lk.y, lk_out.z + Lk.z};
-}
-
-// Reverse of a neighbour's retrace (rk4_g3): its separation uses only
-// G = a1 + a2 + a3, so given lg = dL/dG the adjoints flow through stages 3,
-// 2, 1 (stage 3 sits at p + h/2 (k + h/2 a1), stage 2 at p + h/2 k).  Adds
-// dL/dp and dL/dk of the seed to lp, lk and scatters the n_e nodes.
-__device__ __forceinline__ void rk4_g3_reverse(const GridDev& G, float kf, float h, const Vec& p, const Vec& k,
-                                               const Vec& lg, Vec& lp, Vec& lk, float* dne) {
-  const float hh = 0.5f * h;
-  const Sample s1 = eval_field_t<false>(G, p.x, p.y, p.z, false);
-  const Vec a1{kf * s1.gx, kf * s1.gy, kf * s1.gz};
-  const Vec k2{fmaf(hh, a1.x, k.x), fmaf(hh, a1.y, k.y), fmaf(hh, a1.z, k.z)};
-  // stage 3
-  const Vec Lp3 = force_adjoint(G, kf, fmaf(hh, k2.x, p.x), fmaf(hh, k2.y, p.y), fmaf(hh, k2.z, p.z), lg, dne);
-  // stage 2
-  const Vec Lp2 = force_adjoint(G, kf, fmaf(hh, k.x, p.x), fmaf(hh, k.y, p.y), fmaf(hh, k.z, p.z), lg, dne);
-  // stage 1 (a1 enters G and, through k2, the stage-3 point)
-  const Vec La1{fmaf(hh * hh, Lp3.x, lg.x), fmaf(hh * hh, Lp3.y, lg.y), fmaf(hh * hh, Lp3.z, lg.z)};
-  const Vec Lp1 = force_adjoint(G, kf, p.x, p.y, p.z, La1, dne);
-  lp = {lp.x + Lp1.x + Lp2.x + Lp3.x, lp.y + Lp1.y + Lp2.y + Lp3.y, lp.z + Lp1.z + Lp2.z + Lp3.z};
-  lk = {fmaf(hh, Lp2.x + Lp3.x, lk.x), fmaf(hh, Lp2.y + Lp3.y, lk.y), fmaf(hh, Lp2.z + Lp3.z, lk.z)};
+// Reverse of one RK4 step from (p, k) (rk4_central, or rk4_g3 for a
+// neighbour's retrace), given the adjoints of its outputs: lr = dL/dr',
+// lk = dL/dk' and lg on G = a1 + a2 + a3.  With r' = r + h k + h^2/6 G and
+// k' = k + h/6 (a1 + 2 a2 + 2 a3 + a4), the stage points are
+// P1 = p, P2 = p + h/2 k, P3 = p + h/2 k2, P4 = p + h k3 with
+// k2 = k + h/2 a1, k3 = k + h/2 a2, and a_s = kf grad n_e(P_s).
+// nst = 4 (central ray) or 3 (a neighbour: lr = lk = 0 and the fourth stage
+// has no adjoint).  Adds dL/dp to lp and dL/dk to lko and scatters the n_e
+// nodes.  The stages are reversed in one loop around a single force adjoint
+// (the kernel's instruction footprint, not its arithmetic, bounds it).
+__device__ __forceinline__ void rk4_reverse_any(const GridDev& G, float kf, float h, const Vec& p, const Vec& k,
+                                                const Vec& lr, const Vec& lk, const Vec& lg, int nst, Vec& lp,
+                                                Vec& lko, float* dne) {
+  const float hh = 0.5f * h, h6 = h / 6.f, h3 = h / 3.f;
+  // forward stage points
+  Vec pt[4];
+  pt[0] = p;
+  pt[1] = {fmaf(hh, k.x, p.x), fmaf(hh, k.y, p.y), fmaf(hh, k.z, p.z)};
+#pragma unroll 1
+  for (int s = 0; s < nst - 2; ++s) {  // a1 -> P3; a2 -> P4 (central only)
+    const Sample sm = eval_field_t<false>(G, pt[s].x, pt[s].y, pt[s].z, false);
+    const float c = (s == 0) ? hh : h;
+    const Vec q{fmaf(hh, kf * sm.gx, k.x), fmaf(hh, kf * sm.gy, k.y), fmaf(hh, kf * sm.gz, k.z)};
+    pt[s + 2] = {fmaf(c, q.x, p.x), fmaf(c, q.y, p.y), fmaf(c, q.z, p.z)};
+  }
+  // adjoints of the accelerations and velocities from the outputs
+  // (k4 = k + h a3 enters r' only: its adjoint h/6 lr is applied at once)
+  Vec la[4];
+  la[0] = {fmaf(h6, lk.x, lg.x), fmaf(h6, lk.y, lg.y), fmaf(h6, lk.z, lg.z)};
+  la[1] = {fmaf(h3, lk.x, lg.x), fmaf(h3, lk.y, lg.y), fmaf(h3, lk.z, lg.z)};
+  la[2] = {fmaf(h * h6, lr.x, la[1].x), fmaf(h * h6, lr.y, la[1].y), fmaf(h * h6, lr.z, la[1].z)};
+  la[3] = {h6 * lk.x, h6 * lk.y, h6 * lk.z};
+  Vec lkv[2] = {{h3 * lr.x, h3 * lr.y, h3 * lr.z}, {h3 * lr.x, h3 * lr.y, h3 * lr.z}};  // k2, k3
+  Vec Lp{lr.x, lr.y, lr.z};
+  Vec Lk{lk.x + 2.f * h6 * lr.x, lk.y + 2.f * h6 * lr.y, lk.z + 2.f * h6 * lr.z};  // k itself and k4 = k + h a3
+#pragma unroll 1
+  for (int s = nst - 1; s >= 0; --s) {
+    const Vec LP = force_adjoint(G, kf, pt[s].x, pt[s].y, pt[s].z, la[s], dne);
+    Lp = {Lp.x + LP.x, Lp.y + LP.y, Lp.z + LP.z};
+    if (s >= 2) {  // P_s = p + c k_{s-1}; k_{s-1} = k + h/2 a_{s-2}
+      const float c = (s == 3) ? h : hh;
+      Vec& kv = lkv[s - 2];
+      kv = {fmaf(c, LP.x, kv.x), fmaf(c, LP.y, kv.y), fmaf(c, LP.z, kv.z)};
+      Lk = {Lk.x + kv.x, Lk.y + kv.y, Lk.z + kv.z};
+      Vec& l = la[s - 2];
+      l = {fmaf(hh, kv.x, l.x), fmaf(hh, kv.y, l.y), fmaf(hh, kv.z, l.z)};
+    } else if (s == 1) {  // P2 = p + h/2 k
+      Lk = {fmaf(hh, LP.x, Lk.x), fmaf(hh, LP.y, Lk.y), fmaf(hh, LP.z, Lk.z)};
+    }
+  }
+  lp = {lp.x + Lp.x, lp.y + Lp.y, lp.z + Lp.z};
+  lko = {lko.x + Lk.x, lko.y + Lk.y, lko.z + Lk.z};
 }
 
 // d kappa_vac / d n_e and d kappa_vac / d T_e (see kappa_vac).
@@ -450,33 +431,51 @@ __global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_rays(const __
     }
 
     // ------------------------------------------------ reverse the segment
-    for (int t = n_s - 1; t >= 0; --t) {
-      const StepRec& rc = R[t];
-      const StepRec& rn = R[t + 1];
+    // Step t (node m = m0 + t): (A) the transfer of segment m and the value
+    // adjoints of node m + 1, (B) the neighbours' retraces of step m, (C) the
+    // central step m.  After the first segment of the ray the loop takes one
+    // more trip (t = -1) for node 0 alone.  Each heavy routine (the value
+    // adjoint, the reverse RK4) has one call site.
+    for (int t = n_s - 1; t >= (seg == 0 ? -1 : 0); --t) {
+      const int tn = (t >= 0) ? t + 1 : 0;  // the node whose value adjoints are scattered
+      const StepRec& rn = R[tn];
       const bool last_step = last_seg && t == n_s - 1;
       const bool clip = last_step && clipped;
-      // (A) transfer of segment m = m0 + t (Eq. 2 front to back, differentiated)
-      const float al = clip ? alpha : 1.f;
-      const float kap_sum = rc.kap + rn.kap;
-      const float dt = 0.5f * kap_sum * P.hrsun * al;
-      const float tbar = 0.5f * (rc.te + rn.te);
-      const float qv = __expf(rc.lns_next - rc.tau);
-      const float ed = __expf(-dt);
-      const float om = one_minus_exp_neg(dt);
-      const float W = tbar * om * qv;
-      const float lDt = lamT * (tbar * ed * qv - Wsuf);
-      const float lTbar = lamT * om * qv;
-      const float lLnM = lamT * (W + Wsuf);
-      Wsuf += W;
-      const float lk_node = 0.5f * P.hrsun * al * lDt;
-      const float lkap_n = lkap + lk_node;
-      const float lte_n = lte + 0.5f * lTbar;
-      const float lalpha = 0.5f * kap_sum * P.hrsun * lDt;
-      // node m+1 is complete: scatter its value adjoints
+      float lam_ne = 0.f, lam_te = 0.f, lalpha = 0.f, lLnM = 0.f, lk_node = 0.f, lTbar = 0.f;
       float dkn, dkt;
       kappa_partials(rn.ne, rn.te, kap_c, ln_f, dkn, dkt);
       if (!P.emission) { dkn = 0.f; dkt = 0.f; }
-      const Vec lpos = value_adjoint(P.G, rn.r[0], rn.r[1], rn.r[2], lkap_n * dkn, lte_n + lkap_n * dkt, P.dne, P.dte);
+      if (t >= 0) {
+        // (A) transfer of segment m (Eq. 2 front to back, differentiated)
+        const StepRec& rc = R[t];
+        const float al = clip ? alpha : 1.f;
+        const float kap_sum = rc.kap + rn.kap;
+        const float dt = 0.5f * kap_sum * P.hrsun * al;
+        const float tbar = 0.5f * (rc.te + rn.te);
+        const float qv = __expf(rc.lns_next - rc.tau);
+        const float ed = __expf(-dt);
+        const float om = one_minus_exp_neg(dt);
+        const float W = tbar * om * qv;
+        const float lDt = lamT * (tbar * ed * qv - Wsuf);
+        lTbar = lamT * om * qv;
+        lLnM = lamT * (W + Wsuf);
+        Wsuf += W;
+        lk_node = 0.5f * P.hrsun * al * lDt;
+        const float lkap_n = lkap + lk_node;
+        const float lte_n = lte + 0.5f * lTbar;
+        lalpha = 0.5f * kap_sum * P.hrsun * lDt;
+        lam_ne = lkap_n * dkn;
+        lam_te = lte_n + lkap_n * dkt;
+      } else {
+        // node 0 on the outer sphere: its transfer values and k0 = n(r0) (-o)
+        lam_ne = lkap * dkn;
+        lam_te = lte + lkap * dkt;
+        const Vec k0{rn.k[0], rn.k[1], rn.k[2]};
+        const float n0 = sqrtf(dot3(k0, k0));
+        if (n0 > 0.f) lam_ne += dot3(Lk, k0) / n0 * kn2 / (2.f * n0);
+      }
+      const Vec lpos = value_adjoint(P.G, rn.r[0], rn.r[1], rn.r[2], lam_ne, lam_te, P.dne, P.dte);
+      if (t < 0) break;
       Vec lpc{0.f, 0.f, 0.f};
       if (clip) {
         lpc = lpos;   // the crossing point closes the path
@@ -486,13 +485,14 @@ __global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_rays(const __
       lkap = lk_node;  // node m, completed by segment m - 1
       lte = 0.5f * lTbar;
 
-      // tube area of step m (Eqs. 9-11, differentiated) and (B) the neighbours
+      // tube area of step m (Eqs. 9-11, differentiated)
+      const StepRec& rc = R[t];
       const Vec dr{rc.dr[0], rc.dr[1], rc.dr[2]};
       Vec slp{0.f, 0.f, 0.f}, slk{0.f, 0.f, 0.f};   // sums of the seed adjoints
       Vec lt{0.f, 0.f, 0.f}, le1{0.f, 0.f, 0.f}, le2{0.f, 0.f, 0.f};
       float leps = 0.f;
-      Vec t3{0.f, 0.f, 0.f}, e1{0.f, 0.f, 0.f}, e2{0.f, 0.f, 0.f};
-      float eps = 0.f;
+      Vec t3{0.f, 0.f, 0.f}, e1{0.f, 0.f, 0.f}, e2{0.f, 0.f, 0.f}, lc1{0.f, 0.f, 0.f}, lc2{0.f, 0.f, 0.f};
+      float eps = 0.f, sc = 0.f;
       if (NB > 0) {
         const float d2n = dot3(dr, dr);
         const float ids = rsqrtf(d2n);
@@ -503,95 +503,89 @@ __global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_rays(const __
         const float lm1 = lLnM * __expf(-rc.lnm);  // d ln(1 + m1) / d m1 = 1 / M
         const Vec c2xt{c2.y * t3.z - c2.z * t3.y, c2.z * t3.x - c2.x * t3.z, c2.x * t3.y - c2.y * t3.x};
         const Vec txc1{t3.y * c1.z - t3.z * c1.y, t3.z * c1.x - t3.x * c1.z, t3.x * c1.y - t3.y * c1.x};
-        const Vec lc1{lm1 * (e1.x + c2xt.x), lm1 * (e1.y + c2xt.y), lm1 * (e1.z + c2xt.z)};
-        const Vec lc2{lm1 * (e2.x + txc1.x), lm1 * (e2.y + txc1.y), lm1 * (e2.z + txc1.z)};
+        lc1 = {lm1 * (e1.x + c2xt.x), lm1 * (e1.y + c2xt.y), lm1 * (e1.z + c2xt.z)};
+        lc2 = {lm1 * (e2.x + txc1.x), lm1 * (e2.y + txc1.y), lm1 * (e2.z + txc1.z)};
         le1 = {lm1 * c1.x, lm1 * c1.y, lm1 * c1.z};
         le2 = {lm1 * c2.x, lm1 * c2.y, lm1 * c2.z};
         lt = {lm1 * (c1.y * c2.z - c1.z * c2.y), lm1 * (c1.z * c2.x - c1.x * c2.z), lm1 * (c1.x * c2.y - c1.y * c2.x)};
         leps = -(dot3(c1, lc1) + dot3(c2, lc2)) / eps;
-        const float sc = P.h2_12 / eps;
-        const Vec rk{rc.k[0], rc.k[1], rc.k[2]};
-        // seeds r_m +- eps e_j with k = k_m; G of a "+" seed enters D_j with +, of a "-" seed with -
+        sc = P.h2_12 / eps;
+      }
+
+      // (B) the neighbours' retraces (q < NB), then (C) the central step (q = NB)
+      const Vec rr{rc.r[0], rc.r[1], rc.r[2]}, rk{rc.k[0], rc.k[1], rc.k[2]};
 #pragma unroll 1
-        for (int q = 0; q < 4; ++q) {
-          const bool first = q < 2;
-          const float sgn = (q & 1) ? -1.f : 1.f;
-          const Vec ev = first ? e1 : e2;
+      for (int q = (NB > 0 ? 0 : NB); q <= NB; ++q) {
+        Vec base = rr, lr_in{0.f, 0.f, 0.f}, lk_in{0.f, 0.f, 0.f}, lg{0.f, 0.f, 0.f};
+        Vec lp_o{0.f, 0.f, 0.f}, lk_o{0.f, 0.f, 0.f};
+        const bool first = q < 2;
+        const float sgn = (q & 1) ? -1.f : 1.f;
+        const Vec ev = first ? e1 : e2;
+        if (q < NB) {
+          // seed r_m +- eps e_j with k = k_m; its G enters D_j with the seed's sign
           const Vec lc = first ? lc1 : lc2;
-          const Vec seed{rc.r[0] + sgn * eps * ev.x, rc.r[1] + sgn * eps * ev.y, rc.r[2] + sgn * eps * ev.z};
-          const Vec lg{sgn * sc * lc.x, sgn * sc * lc.y, sgn * sc * lc.z};
-          Vec lps{0.f, 0.f, 0.f}, lks{0.f, 0.f, 0.f};
-          rk4_g3_reverse(P.G, kf, h, seed, rk, lg, lps, lks, P.dne);
-          slp = {slp.x + lps.x, slp.y + lps.y, slp.z + lps.z};
-          slk = {slk.x + lks.x, slk.y + lks.y, slk.z + lks.z};
-          leps += sgn * dot3(ev, lps);
-          if (first) le1 = {fmaf(sgn * eps, lps.x, le1.x), fmaf(sgn * eps, lps.y, le1.y), fmaf(sgn * eps, lps.z, le1.z)};
-          else le2 = {fmaf(sgn * eps, lps.x, le2.x), fmaf(sgn * eps, lps.y, le2.y), fmaf(sgn * eps, lps.z, le2.z)};
+          base = {rr.x + sgn * eps * ev.x, rr.y + sgn * eps * ev.y, rr.z + sgn * eps * ev.z};
+          lg = {sgn * sc * lc.x, sgn * sc * lc.y, sgn * sc * lc.z};
+        } else {
+          Vec ldr{0.f, 0.f, 0.f};
+          if (NB > 0) {
+            // e2 = t x e1
+            lt = {lt.x + (e1.y * le2.z - e1.z * le2.y), lt.y + (e1.z * le2.x - e1.x * le2.z),
+                  lt.z + (e1.x * le2.y - e1.y * le2.x)};
+            le1 = {le1.x + (le2.y * t3.z - le2.z * t3.y), le1.y + (le2.z * t3.x - le2.x * t3.z),
+                   le1.z + (le2.x * t3.y - le2.y * t3.x)};
+            // e1 = c / |c|, c = a x t
+            const Vec av = (fabsf(t3.z) <= 0.9f) ? Vec{0.f, 0.f, 1.f} : Vec{0.f, 1.f, 0.f};
+            const Vec cv{av.y * t3.z - av.z * t3.y, av.z * t3.x - av.x * t3.z, av.x * t3.y - av.y * t3.x};
+            const float ic = rsqrtf(dot3(cv, cv));
+            const float pe = dot3(e1, le1);
+            const Vec lc{(le1.x - pe * e1.x) * ic, (le1.y - pe * e1.y) * ic, (le1.z - pe * e1.z) * ic};
+            lt = {lt.x + (lc.y * av.z - lc.z * av.y), lt.y + (lc.z * av.x - lc.x * av.z),
+                  lt.z + (lc.x * av.y - lc.y * av.x)};
+            // eps = eta |dr| (Eq. 8); t = dr / |dr| (Eq. 5)
+            const float ids = rsqrtf(dot3(dr, dr));
+            const float lds = (P.eps_fixed > 0.f) ? 0.f : P.eta * leps;
+            const float pt = dot3(t3, lt);
+            ldr = {(lt.x - pt * t3.x) * ids + t3.x * lds, (lt.y - pt * t3.y) * ids + t3.y * lds,
+                   (lt.z - pt * t3.z) * ids + t3.z * lds};
+          }
+          lp_o = slp;
+          lk_o = slk;
+          Vec lr_next = Lr;
+          if (clip) {
+            // crossing point pc = r_m + alpha dr with |pc| = R:
+            // d alpha = -(pc . (d r_m + alpha d dr)) / (pc . dr)
+            const Vec pc{rn.r[0], rn.r[1], rn.r[2]};
+            const float den = dot3(pc, dr);
+            const float la = lalpha + dot3(lpc, dr);
+            const float g = (den != 0.f) ? la / den : 0.f;
+            lp_o = {lp_o.x + lpc.x - g * pc.x, lp_o.y + lpc.y - g * pc.y, lp_o.z + lpc.z - g * pc.z};
+            ldr = {ldr.x + alpha * (lpc.x - g * pc.x), ldr.y + alpha * (lpc.y - g * pc.y),
+                   ldr.z + alpha * (lpc.z - g * pc.z)};
+            lr_next = {0.f, 0.f, 0.f};  // the unclipped node is used only through the chord
+          }
+          // dr = r' - r_m
+          lr_in = {lr_next.x + ldr.x, lr_next.y + ldr.y, lr_next.z + ldr.z};
+          lp_o = {lp_o.x - ldr.x, lp_o.y - ldr.y, lp_o.z - ldr.z};
+          lk_in = Lk;
+        }
+        rk4_reverse_any(P.G, kf, h, base, rk, lr_in, lk_in, lg, (q < NB) ? 3 : 4, lp_o, lk_o, P.dne);
+        if (q < NB) {
+          slp = {slp.x + lp_o.x, slp.y + lp_o.y, slp.z + lp_o.z};
+          slk = {slk.x + lk_o.x, slk.y + lk_o.y, slk.z + lk_o.z};
+          leps += sgn * dot3(ev, lp_o);
+          if (first) le1 = {fmaf(sgn * eps, lp_o.x, le1.x), fmaf(sgn * eps, lp_o.y, le1.y), fmaf(sgn * eps, lp_o.z, le1.z)};
+          else le2 = {fmaf(sgn * eps, lp_o.x, le2.x), fmaf(sgn * eps, lp_o.y, le2.y), fmaf(sgn * eps, lp_o.z, le2.z)};
+        } else {
+          Lr = lp_o;  // node m (its value adjoint joins in the next step back)
+          Lk = lk_o;
         }
       }
-
-      // (C) the central RK4 step m with its chord, basis and eps
-      Vec ldr{0.f, 0.f, 0.f};
-      if (NB > 0) {
-        // e2 = t x e1
-        lt = {lt.x + (e1.y * le2.z - e1.z * le2.y), lt.y + (e1.z * le2.x - e1.x * le2.z),
-              lt.z + (e1.x * le2.y - e1.y * le2.x)};
-        le1 = {le1.x + (le2.y * t3.z - le2.z * t3.y), le1.y + (le2.z * t3.x - le2.x * t3.z),
-               le1.z + (le2.x * t3.y - le2.y * t3.x)};
-        // e1 = c / |c|, c = a x t
-        const Vec av = (fabsf(t3.z) <= 0.9f) ? Vec{0.f, 0.f, 1.f} : Vec{0.f, 1.f, 0.f};
-        const Vec cv{av.y * t3.z - av.z * t3.y, av.z * t3.x - av.x * t3.z, av.x * t3.y - av.y * t3.x};
-        const float ic = rsqrtf(dot3(cv, cv));
-        const float pe = dot3(e1, le1);
-        const Vec lc{(le1.x - pe * e1.x) * ic, (le1.y - pe * e1.y) * ic, (le1.z - pe * e1.z) * ic};
-        lt = {lt.x + (lc.y * av.z - lc.z * av.y), lt.y + (lc.z * av.x - lc.x * av.z),
-              lt.z + (lc.x * av.y - lc.y * av.x)};
-        // eps = eta |dr| (Eq. 8); t = dr / |dr| (Eq. 5)
-        const float ids = rsqrtf(dot3(dr, dr));
-        const float lds = (P.eps_fixed > 0.f) ? 0.f : P.eta * leps;
-        const float pt = dot3(t3, lt);
-        ldr = {(lt.x - pt * t3.x) * ids + t3.x * lds, (lt.y - pt * t3.y) * ids + t3.y * lds,
-               (lt.z - pt * t3.z) * ids + t3.z * lds};
-      }
-      Vec lp_o = slp, lk_o = slk;
-      Vec lr_next = Lr;
-      if (clip) {
-        // crossing point pc = r_m + alpha dr with |pc| = R: d alpha = -(pc . (d r_m + alpha d dr)) / (pc . dr)
-        const Vec pc{rn.r[0], rn.r[1], rn.r[2]};
-        const float den = dot3(pc, dr);
-        const float la = lalpha + dot3(lpc, dr);
-        const float g = (den != 0.f) ? la / den : 0.f;
-        lp_o = {lp_o.x + lpc.x - g * pc.x, lp_o.y + lpc.y - g * pc.y, lp_o.z + lpc.z - g * pc.z};
-        ldr = {ldr.x + alpha * (lpc.x - g * pc.x), ldr.y + alpha * (lpc.y - g * pc.y),
-               ldr.z + alpha * (lpc.z - g * pc.z)};
-        lr_next = {0.f, 0.f, 0.f};  // the unclipped node is used only through the chord
-      }
-      // dr = r' - r_m
-      const Vec lr_in{lr_next.x + ldr.x, lr_next.y + ldr.y, lr_next.z + ldr.z};
-      lp_o = {lp_o.x - ldr.x, lp_o.y - ldr.y, lp_o.z - ldr.z};
-      rk4_reverse(P.G, kf, h, Vec{rc.r[0], rc.r[1], rc.r[2]}, Vec{rc.k[0], rc.k[1], rc.k[2]}, lr_in, Lk,
-                  Vec{0.f, 0.f, 0.f}, lp_o, lk_o, P.dne);
-      Lr = lp_o;  // node m (its value adjoint joins in the next step back)
-      Lk = lk_o;
     }
 
-    // ------------------------------------------------ next segment / launch
-    if (seg == 0) {
-      // node 0 on the outer sphere: its transfer values and k0 = n(r0) (-o)
-      const StepRec& r0 = R[0];
-      float dkn, dkt;
-      kappa_partials(r0.ne, r0.te, kap_c, ln_f, dkn, dkt);
-      if (!P.emission) { dkn = 0.f; dkt = 0.f; }
-      float lam_ne = lkap * dkn;
-      const float lam_te = lte + lkap * dkt;
-      const Vec k0{r0.k[0], r0.k[1], r0.k[2]};
-      const float n0 = sqrtf(dot3(k0, k0));
-      if (n0 > 0.f) lam_ne += dot3(Lk, k0) / n0 * kn2 / (2.f * n0);
-      value_adjoint(P.G, r0.r[0], r0.r[1], r0.r[2], lam_ne, lam_te, P.dne, P.dte);
-      active = false;
-    } else {
-      seg -= 1;
-    }
+    // ------------------------------------------------ next segment / done
+    if (seg == 0) active = false;
+    else seg -= 1;
   }
 }
 

@@ -24,6 +24,8 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kElectronCharge = 4.803204712570263e-10;  // statC
 constexpr double kElectronMass = 9.1093837015e-28;         // g
 constexpr double kRsunCm = 6.957e10;                       // IAU nominal
+constexpr double kSpeedOfLightCmS = 2.99792458e10;
+constexpr double kAuRsun = 1.495978707e13 / 6.957e10;      // 1 AU in R_sun (IAU)
 constexpr double kOuterBand = 1e-6;                        // vacuum beyond r_max (1 + band)
 
 thread_local std::string g_err;
@@ -152,6 +154,40 @@ __global__ void probe_field(const GridDev G, const float* __restrict__ xyz, int 
 // Mean T_b over the pixels whose centre lies within `radius` of the image
 // centre (Sec. 3.4: the near-centre quiet-Sun spectrum); one block per
 // frequency, FP64 sums in a fixed order (deterministic).
+// Beam convolution (Sec. 3.3: maps seen by an interferometer of maximum
+// baseline B): each map is convolved with a circular Gaussian beam of
+// FWHM lambda / B (in R_sun on the image plane at 1 AU), separably, rows then
+// columns, with zero outside the image; the weights of one map are the
+// normalised samples exp(-d^2 / 2 sigma^2) at the pixel offsets within 4 sigma.
+// One thread per output pixel; pass 0 reads src along rows, pass 1 along
+// columns.
+constexpr int kBeamThreads = 256;
+struct BeamParams {
+  int nx, ny;
+  float inv2s2[kMaxFreq];  // 1 / (2 sigma^2), sigma in pixels
+  float norm[kMaxFreq];    // 1 / sum of the map's samples
+  int half[kMaxFreq];      // taps each side (ceil(4 sigma))
+};
+
+__global__ void __launch_bounds__(kBeamThreads) beam_pass(const float* __restrict__ src, float* __restrict__ dst,
+                                                          const __grid_constant__ BeamParams B, int col) {
+  const int f = blockIdx.y;
+  const int n = B.nx * B.ny;
+  const int p = blockIdx.x * kBeamThreads + threadIdx.x;
+  if (p >= n) return;
+  const float* m = src + (size_t)f * n;
+  const int hw = B.half[f];
+  const float a = B.inv2s2[f];
+  const int ix = p % B.nx, iy = p / B.nx;
+  double acc = 0.0;
+  for (int d = -hw; d <= hw; ++d) {
+    const int jx = col ? ix : ix + d, jy = col ? iy + d : iy;
+    if (jx < 0 || jx >= B.nx || jy < 0 || jy >= B.ny) continue;
+    acc += (double)expf(-(float)(d * d) * a) * (double)m[jy * B.nx + jx];
+  }
+  dst[(size_t)f * n + p] = (float)(acc * (double)B.norm[f]);
+}
+
 constexpr int kDiskThreads = 512;
 __global__ void __launch_bounds__(kDiskThreads) disk_mean(const float* __restrict__ tb, int nx, int ny, double x0,
                                                           double dx, double y0, double dy, double r2,
@@ -984,6 +1020,93 @@ rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const dou
   if (mismatch)
     return fail(RT_ERR_ARG, "rt_backward: fwd_diag does not match this forward (%llu rays with other step counts)",
                 mismatch);
+  return RT_OK;
+}
+
+rt_status rt_trace_paths(rt_ctx* ctx, const rt_grid* g, const rt_view* v, double freq_hz, const int* pixels, int n,
+                         const rt_options* o, int cap, rt_path_node* nodes, int* n_nodes, float* tb_out,
+                         rt_ray_diag* diag, void* stream) {
+  if (!ctx || !g || !pixels || !nodes || !n_nodes || !tb_out) return fail(RT_ERR_ARG, "rt_trace_paths: NULL argument");
+  rt_status st = check_view(v);
+  if (st != RT_OK) return st;
+  int nb = 0;
+  st = check_options(o, &nb);
+  if (st != RT_OK) return st;
+  if (is_tube(o)) return fail(RT_ERR_UNSUPPORTED, "rt_trace_paths: step-wise magnification or none");
+  if (n < 1 || n > (1 << 20)) return fail(RT_ERR_ARG, "rt_trace_paths: n = %d (1..2^20)", n);
+  if (cap < 1) return fail(RT_ERR_ARG, "rt_trace_paths: cap = %d", cap);
+  if (bad_freq(freq_hz)) return fail(RT_ERR_ARG, "rt_trace_paths: frequency is not > 0");
+  const long npix = (long)v->nx * v->ny;
+  for (int i = 0; i < n; ++i)
+    if (pixels[i] < 0 || pixels[i] >= npix) return fail(RT_ERR_ARG, "rt_trace_paths: pixel %d out of range", pixels[i]);
+  static_assert(sizeof(PathNode) == sizeof(rt_path_node), "rt_path_node layout");
+  TraceParams P;
+  std::memset(&P, 0, sizeof P);
+  fill_common(P, g, o);
+  P.view = make_view(*v);
+  P.nf = 1;
+  P.freq[0] = make_freq(freq_hz, 0);
+  RT_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  int* d_pix = nullptr;
+  RT_CUDA(cudaMallocAsync(&d_pix, sizeof(int) * n, s));
+  cudaError_t e = cudaMemcpyAsync(d_pix, pixels, sizeof(int) * n, cudaMemcpyHostToDevice, s);
+  PathNode* pn = reinterpret_cast<PathNode*>(nodes);
+  RayDiag* dg = reinterpret_cast<RayDiag*>(diag);
+  const int blocks = (n + 63) / 64;
+  const bool mixed = o->precision == RT_MIXED;
+  if (e == cudaSuccess) {
+#define RT_PATHS(NB)                                                                          \
+    (mixed ? trace_paths<NB, true><<<blocks, 64, 0, s>>>(P, d_pix, n, cap, pn, n_nodes, tb_out, dg) \
+           : trace_paths<NB, false><<<blocks, 64, 0, s>>>(P, d_pix, n, cap, pn, n_nodes, tb_out, dg))
+    switch (nb) {
+      case 0: RT_PATHS(0); break;
+      case 2: RT_PATHS(2); break;
+      case 4: RT_PATHS(4); break;
+      default: RT_PATHS(8); break;
+    }
+#undef RT_PATHS
+    e = cudaGetLastError();
+  }
+  cudaError_t e2 = cudaFreeAsync(d_pix, s);
+  if (e != cudaSuccess || e2 != cudaSuccess)
+    return fail(RT_ERR_CUDA, "rt_trace_paths: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  return RT_OK;
+}
+
+rt_status rt_beam_convolve(const rt_view* v, const float* tb, const double* freqs_hz, int nf, double baseline_m,
+                           float* scratch, float* tb_out, void* stream) {
+  if (!tb || !freqs_hz || !scratch || !tb_out) return fail(RT_ERR_ARG, "rt_beam_convolve: NULL argument");
+  rt_status st = check_view(v);
+  if (st != RT_OK) return st;
+  if (nf < 1 || nf > kMaxFreq) return fail(RT_ERR_ARG, "rt_beam_convolve: nf = %d (1..%d)", nf, kMaxFreq);
+  if (!(baseline_m > 0.0) || !std::isfinite(baseline_m)) return fail(RT_ERR_ARG, "rt_beam_convolve: baseline must be > 0");
+  const double dx = std::fabs(v->x1 - v->x0) / v->nx, dy = std::fabs(v->y1 - v->y0) / v->ny;
+  if (!(dx > 0.0) || std::fabs(dx - dy) > 1e-9 * dx)
+    return fail(RT_ERR_ARG, "rt_beam_convolve: pixels must be square (dx = %g, dy = %g)", dx, dy);
+  BeamParams B;
+  std::memset(&B, 0, sizeof B);
+  B.nx = v->nx;
+  B.ny = v->ny;
+  for (int i = 0; i < nf; ++i) {
+    if (bad_freq(freqs_hz[i])) return fail(RT_ERR_ARG, "frequency %d is not > 0", i);
+    const double fwhm = kSpeedOfLightCmS / freqs_hz[i] / (baseline_m * 100.0) * kAuRsun;  // R_sun
+    const double sigma = fwhm / std::sqrt(8.0 * std::log(2.0)) / dx;                    // pixels
+    const double hw = std::ceil(4.0 * sigma);
+    if (hw > 1 << 20) return fail(RT_ERR_ARG, "rt_beam_convolve: beam of %g pixels is too wide", 2 * hw + 1);
+    const float a = (float)(0.5 / (sigma * sigma));
+    double sum = 0.0;
+    for (int d = -(int)hw; d <= (int)hw; ++d) sum += std::exp(-(double)((float)(d * d) * a));
+    B.half[i] = (int)hw;
+    B.inv2s2[i] = a;
+    B.norm[i] = (float)(1.0 / sum);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = v->nx * v->ny;
+  const dim3 grid((n + kBeamThreads - 1) / kBeamThreads, nf);
+  beam_pass<<<grid, kBeamThreads, 0, s>>>(tb, scratch, B, 0);
+  beam_pass<<<grid, kBeamThreads, 0, s>>>(scratch, tb_out, B, 1);
+  RT_CUDA(cudaGetLastError());
   return RT_OK;
 }
 

@@ -85,6 +85,42 @@ struct RayStart {
   float u, v, sc, nc, nec;       // image-plane point, entry depth, n and n_e at the entry (tube launch)
 };
 
+// The launch of the ray of pixel pix (Sec. 3.2): its image-plane point, the
+// entry point on the outer sphere and k = n(r0) (-o); enter = false for a
+// MISS.
+__device__ __forceinline__ void ray_entry(const TraceParams& P, const ViewDev* V, const FreqDev* F, int pix,
+                                          RayStart& s) {
+  s.enter = false;
+  s.px = s.py = s.pz = s.kx = s.ky = s.kz = 0.f;
+  s.sc = s.nec = 0.f;
+  s.nc = 1.f;
+  const int ix = pix % V->nx, iy = pix / V->nx;
+  s.u = fmaf((float)ix + 0.5f, V->dx, V->x0);
+  s.v = fmaf((float)iy + 0.5f, V->dy, V->y0);
+  const float R = P.G.r_max;
+  const float b2 = fmaf(s.u, s.u, s.v * s.v);
+  bool ok = b2 < R * R;
+  if (ok) {
+    s.sc = sqrtf(fmaf(R, R, -b2));
+    s.px = fmaf(s.u, V->eux, fmaf(s.v, V->evx, s.sc * V->ox));
+    s.py = fmaf(s.u, V->euy, fmaf(s.v, V->evy, s.sc * V->oy));
+    s.pz = fmaf(s.u, V->euz, fmaf(s.v, V->evz, s.sc * V->oz));
+    if (!P.straight) {
+      const Sample s0 = eval_field(P.G, s.px, s.py, s.pz, false);
+      s.nec = s0.ne;
+      const float n2 = fmaf(F->kn2, s0.ne, 1.f);
+      ok = n2 > 0.f;
+      s.nc = ok ? sqrtf(n2) : 0.f;
+    }
+  }
+  s.enter = ok;
+  if (ok) {
+    s.kx = -s.nc * V->ox;
+    s.ky = -s.nc * V->oy;
+    s.kz = -s.nc * V->oz;
+  }
+}
+
 __device__ __forceinline__ RayStart start_ray(const TraceParams& P, unsigned int item) {
   RayStart s;
   int pix;
@@ -123,36 +159,8 @@ __device__ __forceinline__ RayStart start_ray(const TraceParams& P, unsigned int
     }
   }
   s.enter = false;
-  s.px = s.py = s.pz = s.kx = s.ky = s.kz = 0.f;
-  s.u = s.v = s.sc = s.nec = 0.f;
-  s.nc = 1.f;
   if (!s.valid) return s;
-  const ViewDev* V = s.V;
-  const int ix = pix % V->nx, iy = pix / V->nx;
-  s.u = fmaf((float)ix + 0.5f, V->dx, V->x0);
-  s.v = fmaf((float)iy + 0.5f, V->dy, V->y0);
-  const float R = P.G.r_max;
-  const float b2 = fmaf(s.u, s.u, s.v * s.v);
-  bool ok = b2 < R * R;
-  if (ok) {
-    s.sc = sqrtf(fmaf(R, R, -b2));
-    s.px = fmaf(s.u, V->eux, fmaf(s.v, V->evx, s.sc * V->ox));
-    s.py = fmaf(s.u, V->euy, fmaf(s.v, V->evy, s.sc * V->oy));
-    s.pz = fmaf(s.u, V->euz, fmaf(s.v, V->evz, s.sc * V->oz));
-    if (!P.straight) {
-      const Sample s0 = eval_field(P.G, s.px, s.py, s.pz, false);
-      s.nec = s0.ne;
-      const float n2 = fmaf(s.F->kn2, s0.ne, 1.f);
-      ok = n2 > 0.f;
-      s.nc = ok ? sqrtf(n2) : 0.f;
-    }
-  }
-  s.enter = ok;
-  if (ok) {
-    s.kx = -s.nc * V->ox;
-    s.ky = -s.nc * V->oy;
-    s.kz = -s.nc * V->oz;
-  }
+  ray_entry(P, s.V, s.F, pix, s);
   return s;
 }
 

@@ -369,3 +369,120 @@ __global__ void __launch_bounds__(kThreads, kRayMinBlocks) trace_rays(const __gr
 }
 
 }  // namespace rt
+
+namespace rt {
+
+// One node of a recorded ray path (rt_path_node).
+struct PathNode {
+  float r[3];
+  float ln_s;     // ln(S / S_0) at the node
+  float dlns_ds;  // ln M of the step arriving at the node over its chord length (0 at node 0)
+  float tau;      // optical depth from the entry to the node
+  float ne, te;   // the interpolated n_e and T_e at the node
+};
+
+// Ray-fan diagnostics (Sec. 3.2, Figs. 4 and 6): the rays of the given pixels
+// at one frequency, one thread each, stepped exactly as trace_rays steps
+// them (the same step code in the same order), recording every node.
+// The first `cap` nodes of ray i go to path[i * cap ...], its node count to
+// count[i], and its T_b and diagnostics to tb[i] and diag[i].
+template <int NB, bool kMixed>
+__global__ void __launch_bounds__(64) trace_paths(const __grid_constant__ TraceParams P, const int* __restrict__ pix,
+                                                  int n, int cap, PathNode* __restrict__ path, int* __restrict__ count,
+                                                  float* __restrict__ tb, RayDiag* __restrict__ diag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float h = P.h;
+  RayStart rs;
+  rs.V = &P.view;
+  rs.F = &P.freq[0];
+  ray_entry(P, rs.V, rs.F, pix[i], rs);
+  PathNode* out = path + (size_t)i * cap;
+  int nodes = 0;
+  auto record = [&](float x, float y, float z, float lns, float dls, float tau, float ne, float te) {
+    if (nodes < cap) {
+      PathNode& q = out[nodes];
+      q.r[0] = x; q.r[1] = y; q.r[2] = z;
+      q.ln_s = lns; q.dlns_ds = dls; q.tau = tau; q.ne = ne; q.te = te;
+    }
+    ++nodes;
+  };
+  float tb_hi = 0.f, tb_lo = 0.f, tau_hi = 0.f, tau_lo = 0.f, lns_hi = 0.f, lns_lo = 0.f;
+  int step = 0, status = kMiss;
+  float ex = rs.px, ey = rs.py, ez = rs.pz;
+  if (rs.enter) {
+    const float kf = P.straight ? 0.f : rs.F->kf, kap_c = rs.F->kap_c, ln_f = rs.F->ln_f;
+    float px = rs.px, py = rs.py, pz = rs.pz, kx = rs.kx, ky = rs.ky, kz = rs.kz;
+    float rlx = 0.f, rly = 0.f, rlz = 0.f, klx = 0.f, kly = 0.f, klz = 0.f;
+    float kap_prev = 0.f, te_prev = 0.f, dls = 0.f;
+    while (true) {
+      const Rk4Out o = rk4_central(P.G, kf, h, px, py, pz, kx, ky, kz);
+      const float kap = P.emission ? kappa_vac(o.ne1, o.te1, kap_c, ln_f) : 0.f;
+      if (step >= 1) {
+        const float dt = 0.5f * (kap_prev + kap) * P.hrsun;
+        const float tbar = 0.5f * (te_prev + o.te1);
+        const float tau0 = tau_hi + tau_lo;
+        acc_add<kMixed>(tb_hi, tb_lo, tbar * one_minus_exp_neg(dt) * __expf((lns_hi + lns_lo) - tau0));
+        acc_add<kMixed>(tau_hi, tau_lo, dt);
+      }
+      record(px, py, pz, lns_hi + lns_lo, dls, tau_hi + tau_lo, o.ne1, o.te1);
+      ex = px; ey = py; ez = pz;
+      if (step >= 1 && P.tau_stop > 0.f && tau_hi + tau_lo >= P.tau_stop) { status = kTauStop; break; }
+      if (step >= 1 && step >= P.max_steps) { status = kStepLimit; break; }
+      Vec dr, rn, kn;
+      complete_step<kMixed>(h, P.h2_6, P.h_6, o, px, py, pz, kx, ky, kz, rlx, rly, rlz, klx, kly, klz, dr, rn, kn);
+      kap_prev = kap;
+      te_prev = o.te1;
+      const float rr2 = dot3(rn, rn);
+      int term = 0;
+      if (rr2 < P.G.r_min * P.G.r_min) term = kHitInner;
+      else if (rr2 > P.G.r_max * P.G.r_max && dot3(rn, kn) > 0.f) term = kExitOuter;
+      else if (!isfinite(rr2 + kn.x + kn.y + kn.z)) term = kNan;
+      dls = 0.f;
+      if (NB > 0 && term != kNan) {
+        const Retrace R = retrace_step<(NB > 0 ? NB : 4)>(P.G, kf, h, P.h2_6, P.h2_12, P.eta, P.eps_fixed, px, py,
+                                                          pz, kx, ky, kz, dr, Vec{o.Gx, o.Gy, o.Gz});
+        acc_add<kMixed>(lns_hi, lns_lo, R.lm);
+        dls = R.lm * rsqrtf(dot3(dr, dr));
+      }
+      if (term == 0) {
+        px = rn.x; py = rn.y; pz = rn.z;
+        kx = kn.x; ky = kn.y; kz = kn.z;
+        step += 1;
+        continue;
+      }
+      step += 1;
+      status = term;
+      if (term == kNan) { ex = rn.x; ey = rn.y; ez = rn.z; break; }
+      const Vec here{px, py, pz};
+      const float a = chord_crossing(here, dr, (term == kHitInner) ? P.G.r_min : P.G.r_max, term == kExitOuter);
+      const float cx = fmaf(a, dr.x, px), cy = fmaf(a, dr.y, py), cz = fmaf(a, dr.z, pz);
+      const Sample s = eval_field(P.G, cx, cy, cz, true);
+      const float kap_e = P.emission ? kappa_vac(s.ne, s.te, kap_c, ln_f) : 0.f;
+      const float dt = 0.5f * (kap_prev + kap_e) * P.hrsun * a;
+      const float tbar = 0.5f * (te_prev + s.te);
+      const float lns = lns_hi + lns_lo;
+      acc_add<kMixed>(tb_hi, tb_lo, tbar * one_minus_exp_neg(dt) * __expf(lns - (tau_hi + tau_lo)));
+      acc_add<kMixed>(tau_hi, tau_lo, dt);
+      float tbc = 0.f;
+      if (term == kHitInner) tbc = (P.tbc_mode == 1) ? P.tbc_K : s.te;
+      if (tbc != 0.f) acc_add<kMixed>(tb_hi, tb_lo, tbc * __expf(lns - (tau_hi + tau_lo)));
+      record(cx, cy, cz, lns, dls, tau_hi + tau_lo, s.ne, s.te);
+      ex = cx; ey = cy; ez = cz;
+      break;
+    }
+  }
+  count[i] = nodes;
+  tb[i] = tb_hi + tb_lo;
+  if (diag) {
+    RayDiag d;
+    d.exit_pos[0] = ex; d.exit_pos[1] = ey; d.exit_pos[2] = ez;
+    d.tau = tau_hi + tau_lo;
+    d.ln_s = lns_hi + lns_lo;
+    d.steps = step;
+    d.status = status;
+    diag[i] = d;
+  }
+}
+
+}  // namespace rt

@@ -60,3 +60,24 @@ def test_disk_mean_spectrum_traced(rt, ctx, orc):
         ref = orc.trace(orc.grid_field(g), v, f, orc.default_options(tau_stop=30.0, **opt))["tb"]
         want = orc.disk_mean_tb(v, ref, 0.5)
         assert np.all(np.abs(got - want) <= 1e-3 * want), (opt, got, want)
+
+
+@pytest.mark.parametrize("baseline", [15e3, 5e3])
+def test_beam_convolution(rt, ctx, orc, baseline):
+    """rt_beam_convolve against the oracle's plain separable convolution: on
+    random maps of a ragged view at three frequencies (beam sigmas from 0.5 to
+    27 pixels, edges included), and on traced maps of the tiny corona."""
+    import torch
+    v = cs.View(0.0, 0.0, 121, 81, -0.3025, 0.3025, -0.2025, 0.2025)   # square pixels of 0.005 R_sun
+    f = np.array([40e6, 150e6, 800e6])
+    rng = np.random.default_rng(8)
+    maps = rng.uniform(0.0, 1e6, size=(3, v.ny, v.nx)).astype(np.float32)
+    got = ctx.beam_convolve(v, torch.from_numpy(maps).cuda(), f, baseline).cpu().numpy()
+    want = orc.beam_convolve(v, maps.astype(np.float64), f, baseline)
+    assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
+    g, _, _ = cs.tiny_workload()
+    grid = ctx.load(g)
+    tb = ctx.trace_image(grid, v, f, rt.options(precision=1))
+    got = ctx.beam_convolve(v, tb, f, baseline).cpu().numpy()
+    want = orc.beam_convolve(v, tb.cpu().numpy().astype(np.float64), f, baseline)
+    assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()

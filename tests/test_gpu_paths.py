@@ -1,0 +1,96 @@
+"""Ray-fan diagnostics on the GPU (rt_trace_paths; Sec. 3.2 Figs. 4 and 6,
+Sec. 3.3): recorded paths against the oracle's, the T_b and diagnostics of
+the recorded rays against rt_trace_image, and the qualitative claims and
+step dependence the paper's figures rest on."""
+import numpy as np
+import pytest
+
+import corona_synth as cs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_02413_gb300 import build
+    build.build()
+    import paper_2606_02413_gb300 as rt
+    return rt
+
+
+@pytest.fixture(scope="module")
+def ctx(rt):
+    return rt.Context(0)
+
+
+FAN = cs.View(0.0, 0.0, 9, 1, -2.2, 2.2, 0.3, 0.31)   # a row of rays across the disk and both limbs
+
+
+def test_paths_match_oracle_and_trace(rt, ctx, orc):
+    """Every node of the recorded paths of the symmetric corona within 1e-4
+    R_sun of the oracle's (same node count), ln S within 1e-4, n_e within
+    1e-5 relative, T_e exact; the rays' T_b and diagnostics bit-identical to
+    rt_trace_image's."""
+    import torch
+    g, _, _ = cs.tiny_workload()
+    grid = ctx.load(g)
+    pix = np.arange(FAN.nx, dtype=np.int32)
+    o = rt.options(precision=1)
+    paths, tb, d = ctx.trace_paths(grid, FAN, 60e6, pix, o)
+    tb_img, d_img = ctx.trace_image(grid, FAN, [60e6], o, diag=True)
+    torch.cuda.synchronize()
+    assert torch.equal(tb, tb_img.reshape(-1)) and torch.equal(d, d_img.reshape(-1, 7))
+    F = orc.grid_field(g)
+    for p, gp in zip(pix, paths):
+        ref = orc.trace_path(F, FAN, 60e6, int(p), orc.default_options(tau_stop=30.0))
+        assert gp["n_nodes"] == ref["n_nodes"], (p, gp["n_nodes"], ref["n_nodes"])
+        assert np.abs(gp["r"] - ref["r"]).max() <= 1e-4
+        assert np.abs(gp["ln_s"] - ref["ln_s_path"]).max() <= 1e-4
+        assert np.allclose(gp["ne"], ref["ne"], rtol=1e-5, atol=0.0)
+        assert np.allclose(gp["te"], ref["te"], rtol=1e-6)
+
+
+def test_fan_bends_outward_and_magnification_rates(rt, ctx):
+    """Refraction keeps rays out of the dense corona: each ray's closest
+    approach to the Sun's centre lies above its impact parameter (the
+    straight line's closest approach).  The magnification rate d ln S/ds and
+    S/S_0 along a 60 MHz fan of the headline corona are reported (the paper
+    quotes d ln S/ds < ~0.4 R_sun^-1 and |S/S_0 - 1| ~ 6% on its MAS model)."""
+    g, _, _ = cs.tiny_workload()
+    grid = ctx.load(g)
+    paths, _, _ = ctx.trace_paths(grid, FAN, 60e6, np.arange(FAN.nx, dtype=np.int32), rt.options(precision=1))
+    u = FAN.x0 + (np.arange(FAN.nx) + 0.5) * (FAN.x1 - FAN.x0) / FAN.nx
+    b = np.hypot(u, 0.5 * (FAN.y0 + FAN.y1))
+    for bi, p in zip(b, paths):
+        assert np.linalg.norm(p["r"], axis=1).min() > bi
+    gg, v, f = cs.global_workload()
+    grid_g = ctx.load(gg)
+    fan = cs.View(0.0, 0.0, 16, 1, -2.0, 2.0, 0.0, 6.0 / 512)
+    paths, _, _ = ctx.trace_paths(grid_g, fan, 60e6, np.arange(16, dtype=np.int32), rt.options(precision=1))
+    rate = max(np.abs(p["dlns_ds"]).max() for p in paths)
+    s_dev = max(np.abs(np.expm1(p["ln_s"])).max() for p in paths)
+    print(f"headline corona, 60 MHz fan: max |d ln S/ds| = {rate:.3f} / R_sun, max |S/S_0 - 1| = {s_dev:.3%}")
+    assert np.isfinite(rate) and rate < 10.0 and s_dev < 1.0
+
+
+def test_stepwise_magnification_is_first_order_in_the_step(rt, ctx, orc):
+    """Reading of Eqs. 5-11 (per step M - 1 ~ h^2, so ln(S_N / S_0) ~ h): the
+    GPU's ln S of the outer rays of the fan halves with the step, as the
+    oracle's does (ratio between 1.7 and 2.3 per halving)."""
+    import torch
+    g, _, _ = cs.tiny_workload()
+    grid = ctx.load(g)
+    lns = {}
+    for h in (4e-3, 2e-3, 1e-3):
+        _, d = ctx.trace_image(grid, FAN, [60e6], rt.options(precision=1, dtau=h), diag=True)
+        torch.cuda.synchronize()
+        lns[h] = rt.diag_to_numpy(d)["ln_s"].reshape(-1)
+    ref = orc.trace(orc.grid_field(g), FAN, [60e6], orc.default_options(dtau=2e-3, tau_stop=30.0))["ln_s"][0]
+    print("ln S at h = 4e-3, 2e-3, 1e-3:", {h: np.round(a, 6).tolist() for h, a in lns.items()})
+    for i in (0, 1, 7, 8):
+        r1, r2 = lns[4e-3][i] / lns[2e-3][i], lns[2e-3][i] / lns[1e-3][i]
+        assert 1.7 < r1 < 2.3 and 1.7 < r2 < 2.3, (i, r1, r2)
+        assert abs(lns[2e-3][i] - ref[i]) <= 1e-4

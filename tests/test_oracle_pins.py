@@ -653,3 +653,30 @@ def test_disk_mean_closed_forms(orc):
     assert orc.disk_mean_tb(v, rho2[None], 0.5)[0] == pytest.approx(0.125, rel=2e-3)
     assert orc.disk_mean_tb(v, rho2[None], 1e-4)[0] == 0.0
 
+
+def test_beam_convolution_closed_forms(orc):
+    """Beam convolution (Sec. 3.3): the beam of a 15 km baseline at 100 MHz
+    has FWHM lambda / B = 41.2 arcsec, which at 1 AU is 41.2 / 959.63 R_sun
+    (959.63 arcsec: the Sun's angular radius at 1 AU, an independent
+    constant); a point source becomes the normalised separable Gaussian with
+    variance sigma^2 per axis; a constant map keeps its value away from the
+    image edges."""
+    v = cs.View(0.0, 0.0, 201, 201, -1.005, 1.005, -1.005, 1.005)   # 0.01 R_sun pixels
+    lam_m = 2.99792458e8 / 100e6
+    fwhm_rsun = lam_m / 15e3 * 206264.806 / 959.63
+    sigma = orc.beam_sigma_pixels(v, 100e6, 15e3)
+    # to 1e-3: 959.63 arcsec corresponds to R_sun = 6.960e8 m, 4e-4 above the IAU nominal radius used here
+    assert sigma * math.sqrt(8 * math.log(2)) * 0.01 == pytest.approx(fwhm_rsun, rel=1e-3)
+    delta = np.zeros((1, 201, 201))
+    delta[0, 100, 100] = 1.0
+    out = orc.beam_convolve(v, delta, [100e6], 15e3)[0]
+    assert out.sum() == pytest.approx(1.0, rel=1e-12)
+    d = np.arange(201) - 100.0
+    var_x = (out.sum(axis=0) * d * d).sum()
+    assert var_x == pytest.approx(sigma * sigma, rel=1e-3)
+    assert np.allclose(out, np.outer(out[:, 100] / out[100, 100], out[100, :]), rtol=1e-10, atol=1e-18)
+    flat = orc.beam_convolve(v, np.full((1, 201, 201), 7.0), [100e6], 15e3)[0]
+    hw = int(math.ceil(4 * sigma))
+    assert np.allclose(flat[hw:-hw, hw:-hw], 7.0, rtol=1e-12)
+    assert flat[0, 0] < 7.0
+
