@@ -123,20 +123,23 @@ def dist_env():
     return ws, rank, local
 
 
+FORWARD_SOURCES = ("rt_device.cuh", "rt_bundle.cuh", "rt_rays.cuh")
+
+
 def kernel_source_hash() -> str:
-    """Hash of the CUDA sources (file names and contents) the library is
-    built from: a committed counter capture is valid only for this hash."""
-    import glob
+    """Hash of the device sources of the headline kernel (trace_rays: file
+    names and contents): a committed counter capture is valid only for this
+    hash."""
     import hashlib
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2606_02413_gb300", "csrc", "*.cu*"))):
-        h.update(os.path.basename(p).encode())
-        with open(p, "rb") as fh:
+    for name in FORWARD_SOURCES:
+        h.update(name.encode())
+        with open(os.path.join(ROOT, "paper_2606_02413_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "trace_bundles_global_512x512x16_launches.md")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "trace_rays_global_512x512x16_launches.md")
 
 
 def committed_traffic():
@@ -351,7 +354,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--profile-case", default=None,
-                    choices=["fwd-128x128x2", "fwd-256x256x2", "fwd-256x256x8", "fwd-256x256x16", "adj-64x64x2",
+                    choices=["fwd-128x128x2", "fwd-256x256x2", "fwd-256x256x8", "fwd-256x256x16", "fwd-512x512x2",
+                             "adj-64x64x2",
                              "adj-128x128x8", "adj-256x256x8"],
                     help="run one launch of a small named case (for ncu captures) and exit")
     ap.add_argument("--no-adjoint", action="store_true")

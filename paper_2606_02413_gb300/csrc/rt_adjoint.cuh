@@ -202,38 +202,42 @@ __device__ __forceinline__ void rk4_reverse_any(const GridDev& G, float kf, floa
                                                 const Vec& lr, const Vec& lk, const Vec& lg, int nst, Vec& lp,
                                                 Vec& lko, float* dne) {
   const float hh = 0.5f * h, h6 = h / 6.f, h3 = h / 3.f;
-  // forward stage points
-  Vec pt[4];
-  pt[0] = p;
-  pt[1] = {fmaf(hh, k.x, p.x), fmaf(hh, k.y, p.y), fmaf(hh, k.z, p.z)};
-#pragma unroll 1
-  for (int s = 0; s < nst - 2; ++s) {  // a1 -> P3; a2 -> P4 (central only)
-    const Sample sm = eval_field_t<false>(G, pt[s].x, pt[s].y, pt[s].z, false);
-    const float c = (s == 0) ? hh : h;
-    const Vec q{fmaf(hh, kf * sm.gx, k.x), fmaf(hh, kf * sm.gy, k.y), fmaf(hh, kf * sm.gz, k.z)};
-    pt[s + 2] = {fmaf(c, q.x, p.x), fmaf(c, q.y, p.y), fmaf(c, q.z, p.z)};
+  // forward stage points (kept in registers: the stage loop selects among them)
+  const Vec P2{fmaf(hh, k.x, p.x), fmaf(hh, k.y, p.y), fmaf(hh, k.z, p.z)};
+  Vec P3, P4{0.f, 0.f, 0.f};
+  {
+    const Sample s1 = eval_field_t<false>(G, p.x, p.y, p.z, false);
+    const Vec q{fmaf(hh, kf * s1.gx, k.x), fmaf(hh, kf * s1.gy, k.y), fmaf(hh, kf * s1.gz, k.z)};
+    P3 = {fmaf(hh, q.x, p.x), fmaf(hh, q.y, p.y), fmaf(hh, q.z, p.z)};
+  }
+  if (nst == 4) {
+    const Sample s2 = eval_field_t<false>(G, P2.x, P2.y, P2.z, false);
+    const Vec q{fmaf(hh, kf * s2.gx, k.x), fmaf(hh, kf * s2.gy, k.y), fmaf(hh, kf * s2.gz, k.z)};
+    P4 = {fmaf(h, q.x, p.x), fmaf(h, q.y, p.y), fmaf(h, q.z, p.z)};
   }
   // adjoints of the accelerations and velocities from the outputs
   // (k4 = k + h a3 enters r' only: its adjoint h/6 lr is applied at once)
-  Vec la[4];
-  la[0] = {fmaf(h6, lk.x, lg.x), fmaf(h6, lk.y, lg.y), fmaf(h6, lk.z, lg.z)};
-  la[1] = {fmaf(h3, lk.x, lg.x), fmaf(h3, lk.y, lg.y), fmaf(h3, lk.z, lg.z)};
-  la[2] = {fmaf(h * h6, lr.x, la[1].x), fmaf(h * h6, lr.y, la[1].y), fmaf(h * h6, lr.z, la[1].z)};
-  la[3] = {h6 * lk.x, h6 * lk.y, h6 * lk.z};
-  Vec lkv[2] = {{h3 * lr.x, h3 * lr.y, h3 * lr.z}, {h3 * lr.x, h3 * lr.y, h3 * lr.z}};  // k2, k3
+  Vec La1{fmaf(h6, lk.x, lg.x), fmaf(h6, lk.y, lg.y), fmaf(h6, lk.z, lg.z)};
+  Vec La2{fmaf(h3, lk.x, lg.x), fmaf(h3, lk.y, lg.y), fmaf(h3, lk.z, lg.z)};
+  Vec La3{fmaf(h * h6, lr.x, La2.x), fmaf(h * h6, lr.y, La2.y), fmaf(h * h6, lr.z, La2.z)};
+  const Vec La4{h6 * lk.x, h6 * lk.y, h6 * lk.z};
+  Vec Lk2{h3 * lr.x, h3 * lr.y, h3 * lr.z}, Lk3 = Lk2;  // adjoints of k2, k3
   Vec Lp{lr.x, lr.y, lr.z};
   Vec Lk{lk.x + 2.f * h6 * lr.x, lk.y + 2.f * h6 * lr.y, lk.z + 2.f * h6 * lr.z};  // k itself and k4 = k + h a3
 #pragma unroll 1
   for (int s = nst - 1; s >= 0; --s) {
-    const Vec LP = force_adjoint(G, kf, pt[s].x, pt[s].y, pt[s].z, la[s], dne);
+    const Vec pt = (s == 3) ? P4 : (s == 2) ? P3 : (s == 1) ? P2 : p;
+    const Vec la = (s == 3) ? La4 : (s == 2) ? La3 : (s == 1) ? La2 : La1;
+    const Vec LP = force_adjoint(G, kf, pt.x, pt.y, pt.z, la, dne);
     Lp = {Lp.x + LP.x, Lp.y + LP.y, Lp.z + LP.z};
-    if (s >= 2) {  // P_s = p + c k_{s-1}; k_{s-1} = k + h/2 a_{s-2}
-      const float c = (s == 3) ? h : hh;
-      Vec& kv = lkv[s - 2];
-      kv = {fmaf(c, LP.x, kv.x), fmaf(c, LP.y, kv.y), fmaf(c, LP.z, kv.z)};
-      Lk = {Lk.x + kv.x, Lk.y + kv.y, Lk.z + kv.z};
-      Vec& l = la[s - 2];
-      l = {fmaf(hh, kv.x, l.x), fmaf(hh, kv.y, l.y), fmaf(hh, kv.z, l.z)};
+    if (s == 3) {         // P4 = p + h k3, k3 = k + h/2 a2
+      Lk3 = {fmaf(h, LP.x, Lk3.x), fmaf(h, LP.y, Lk3.y), fmaf(h, LP.z, Lk3.z)};
+      Lk = {Lk.x + Lk3.x, Lk.y + Lk3.y, Lk.z + Lk3.z};
+      La2 = {fmaf(hh, Lk3.x, La2.x), fmaf(hh, Lk3.y, La2.y), fmaf(hh, Lk3.z, La2.z)};
+    } else if (s == 2) {  // P3 = p + h/2 k2, k2 = k + h/2 a1
+      Lk2 = {fmaf(hh, LP.x, Lk2.x), fmaf(hh, LP.y, Lk2.y), fmaf(hh, LP.z, Lk2.z)};
+      Lk = {Lk.x + Lk2.x, Lk.y + Lk2.y, Lk.z + Lk2.z};
+      La1 = {fmaf(hh, Lk2.x, La1.x), fmaf(hh, Lk2.y, La1.y), fmaf(hh, Lk2.z, La1.z)};
     } else if (s == 1) {  // P2 = p + h/2 k
       Lk = {fmaf(hh, LP.x, Lk.x), fmaf(hh, LP.y, Lk.y), fmaf(hh, LP.z, Lk.z)};
     }
@@ -438,7 +442,9 @@ __global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_rays(const __
     // adjoint, the reverse RK4) has one call site.
     for (int t = n_s - 1; t >= (seg == 0 ? -1 : 0); --t) {
       const int tn = (t >= 0) ? t + 1 : 0;  // the node whose value adjoints are scattered
-      const StepRec& rn = R[tn];
+      // this step's two records, read once at the top of the trip
+      const StepRec rn = R[tn];
+      const StepRec rc = R[max(t, 0)];
       const bool last_step = last_seg && t == n_s - 1;
       const bool clip = last_step && clipped;
       float lam_ne = 0.f, lam_te = 0.f, lalpha = 0.f, lLnM = 0.f, lk_node = 0.f, lTbar = 0.f;
@@ -447,7 +453,6 @@ __global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_rays(const __
       if (!P.emission) { dkn = 0.f; dkt = 0.f; }
       if (t >= 0) {
         // (A) transfer of segment m (Eq. 2 front to back, differentiated)
-        const StepRec& rc = R[t];
         const float al = clip ? alpha : 1.f;
         const float kap_sum = rc.kap + rn.kap;
         const float dt = 0.5f * kap_sum * P.hrsun * al;
@@ -486,7 +491,6 @@ __global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_rays(const __
       lte = 0.5f * lTbar;
 
       // tube area of step m (Eqs. 9-11, differentiated)
-      const StepRec& rc = R[t];
       const Vec dr{rc.dr[0], rc.dr[1], rc.dr[2]};
       Vec slp{0.f, 0.f, 0.f}, slk{0.f, 0.f, 0.f};   // sums of the seed adjoints
       Vec lt{0.f, 0.f, 0.f}, le1{0.f, 0.f, 0.f}, le2{0.f, 0.f, 0.f};

@@ -523,7 +523,10 @@ struct ChunkDev {
 
 // Forward state at the start of every kCkptEvery-th central step, written
 // (optionally) by the forward kernel for the adjoint's recomputation.
-constexpr int kCkptEvery = 32;
+#ifndef RT_CKPT_EVERY
+#define RT_CKPT_EVERY 32
+#endif
+constexpr int kCkptEvery = RT_CKPT_EVERY;
 struct Ckpt {
   float r[3], k[3], rl[3], kl[3];
   float tau_hi, tau_lo, lns_hi, lns_lo;
