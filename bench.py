@@ -123,18 +123,18 @@ def dist_env():
     return ws, rank, local
 
 
-FORWARD_SOURCES = ("rt_device.cuh", "rt_bundle.cuh", "rt_rays.cuh")
+FORWARD_SOURCES = ("csrc/rt_device.cuh", "csrc/rt_bundle.cuh", "csrc/rt_rays.cuh", "build.py")
 
 
 def kernel_source_hash() -> str:
-    """Hash of the device sources of the headline kernel (trace_rays: file
-    names and contents): a committed counter capture is valid only for this
-    hash."""
+    """Hash of what the headline kernel (trace_rays) is compiled from: its
+    device sources and the build script with its compiler flags (file names
+    and contents).  A committed counter capture is valid only for this hash."""
     import hashlib
     h = hashlib.sha256()
     for name in FORWARD_SOURCES:
         h.update(name.encode())
-        with open(os.path.join(ROOT, "paper_2606_02413_gb300", "csrc", name), "rb") as fh:
+        with open(os.path.join(ROOT, "paper_2606_02413_gb300", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 

@@ -377,7 +377,8 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
   if (nr < 2 || nt < 2 || np < 2) return fail(RT_ERR_GRID, "rt_load_grid: need >= 2 nodes per axis");
   if (!d->r_nodes || !d->theta_nodes || !d->phi_nodes) return fail(RT_ERR_ARG, "rt_load_grid: NULL node array");
   const long nodes = (long)nr * nt * np;
-  if ((long)(nr - 1) * (nt - 1) * np > (1L << 31) / 2) return fail(RT_ERR_GRID, "rt_load_grid: grid too large");
+  // cells, with the vacuum shell, must index as 2 * cell in 32 bits
+  if ((long)nr * (nt - 1) * np > (1L << 31) / 2) return fail(RT_ERR_GRID, "rt_load_grid: grid too large");
   const double* R = d->r_nodes;
   const double* T = d->theta_nodes;
   const double* Ph = d->phi_nodes;
@@ -409,6 +410,9 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
   std::vector<float2> rcell(nr - 1);
   for (int i = 0; i + 1 < nr; ++i)
     rcell[i] = make_float2(Rf[i], (float)(1.0 / ((double)Rf[i + 1] - (double)Rf[i])));
+  // vacuum beyond r_vac: the lookup's "up" test r >= r_vac_split holds exactly for r > r_vac
+  const float r_vac_f = (float)(R[nr - 1] * (1.0 + kOuterBand));
+  const float r_vac_split = std::nextafter(r_vac_f, std::numeric_limits<float>::infinity());
   std::vector<RadBin> lut(nb);
   for (int b = 0; b < nb; ++b) {
     const double lo = (double)Rf[0] + b * bw, hi = lo + bw;
@@ -424,6 +428,11 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
     if (base + 1 <= nr - 2 && (double)Rf[base + 1] < hi) {
       e.split = Rf[base + 1];
       e.inv1 = rcell[base + 1].y;
+    } else if (base == nr - 2) {
+      // the last cell's bins (and, by the index clamp, every radius beyond
+      // them) switch to the all-zero shell nr - 1 above r_vac: vacuum
+      e.split = r_vac_split;
+      e.inv1 = 0.f;
     }
     lut[b] = e;
   }
@@ -455,8 +464,9 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
     }
   };
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMalloc(&g->ne, sizeof(float4) * 2 * ncell);
-  if (e == cudaSuccess) e = cudaMalloc(&g->te, sizeof(float4) * 2 * ncell);
+  const long nshell = (long)(nt - 1) * np;  // cells of one radial shell
+  if (e == cudaSuccess) e = cudaMalloc(&g->ne, sizeof(float4) * 2 * (ncell + nshell));
+  if (e == cudaSuccess) e = cudaMalloc(&g->te, sizeof(float4) * 2 * (ncell + nshell));
   if (e == cudaSuccess) e = cudaMalloc(&g->lut, sizeof(RadBin) * nb);
   if (e == cudaSuccess) e = cudaMalloc(&g->rcell, sizeof(float2) * (nr - 1));
   if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(unsigned int));
@@ -480,6 +490,9 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
   if (e == cudaSuccess) e = cudaMemcpyAsync(g->lut, lut.data(), sizeof(RadBin) * nb, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(g->rcell, rcell.data(), sizeof(float2) * (nr - 1), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned int), s);
+  // the vacuum shell (cells nr - 1): all corners zero
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->ne + 2 * ncell, 0, sizeof(float4) * 2 * nshell, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->te + 2 * ncell, 0, sizeof(float4) * 2 * nshell, s);
   const int blocks = ctx->sm_count * 8;
   if (e == cudaSuccess) {
     if (d->dtype == RT_F64) {
@@ -519,7 +532,7 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
   G.r_lut_inv = (float)(nb / span);
   G.r_min = Rf[0];
   G.r_max = Rf[nr - 1];
-  G.r_vac = (float)(R[nr - 1] * (1.0 + kOuterBand));
+  G.r_vac = r_vac_f;
   G.t0 = (float)T[0];
   G.t_inv = (float)(1.0 / dth);
   G.t_last = (float)(nt - 1);

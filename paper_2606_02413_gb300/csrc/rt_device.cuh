@@ -26,7 +26,9 @@ constexpr int kMinBlocksTube = 6;          // tube bundles: the offset evaluatio
 // the narrowest cell, so at most one node lies inside a bin; a bin holds
 // everything one lookup needs in one 32-byte sector: the cell at its lower
 // edge, the node inside it (or +inf), and the base radius and inverse width
-// of the two cells it can select.
+// of the two cells it can select.  Cells i = n_r - 1 form an all-zero shell:
+// the last cell's bins (and every radius beyond them) select it above r_vac,
+// so a lookup there yields n_e = T_e = 0 and a zero gradient (vacuum).
 struct __align__(32) RadBin {
   int base;     // cell at the bin's lower edge
   float split;  // R_{base+1} when that node lies inside the bin, else +inf
@@ -171,7 +173,7 @@ __device__ __forceinline__ Sample eval_field_t(const GridDev& G, float x, float 
   const float r2 = fmaf(z, z, rho2);
   const float inv_r = rsqrtf(r2);
   const float r = r2 * inv_r;
-  if (!(r <= G.r_vac)) return vacuum_sample();  // beyond the outer band (and NaN positions)
+  // beyond r_vac the radial lookup selects the all-zero shell: vacuum, exactly
   float R, inv_dr;
   const int i = radial_lookup(G, r, R, inv_dr);
   const float u = (r - R) * inv_dr;

@@ -228,29 +228,29 @@ __global__ void __launch_bounds__(kThreads, kRayMinBlocks) trace_rays(const __gr
     active = false;
   };
 
-  // one central step of this thread's bundle
+  // One central step of this thread's bundle.  Every lane of the warp runs
+  // it while any lane holds a ray: a lane without one (only when the ticket
+  // pool is exhausted) computes on its stale state, whose lookups stay in
+  // bounds, and writes nothing.  Keeping the evaluations out of divergent
+  // branches lets warp-uniform values (grid and step parameters) live in
+  // uniform registers.
   auto step_once = [&]() {
     // ---------------------------------------------- (a) central RK4 step
     const Rk4Out o = rk4_central(P.G, kf, h, px, py, pz, kx, ky, kz);
     const float kap = P.emission ? kappa_vac(o.ne1, o.te1, kap_c, ln_f) : 0.f;
 
     // ---------------------------------------------- (b) segment step-1 -> step
+    int stop = 0;  // TAU_STOP or STEP_LIMIT: the path ends at node `step`
     if (step >= 1) {
       const float dt = 0.5f * (kap_prev + kap) * P.hrsun;
       const float tbar = 0.5f * (te_prev + o.te1);
       const float tau0 = tau_hi + tau_lo;
       acc_add<kMixed>(tb_hi, tb_lo, tbar * one_minus_exp_neg(dt) * __expf((lns_hi + lns_lo) - tau0));
       acc_add<kMixed>(tau_hi, tau_lo, dt);
-      if (P.tau_stop > 0.f && tau_hi + tau_lo >= P.tau_stop) {
-        finish(kTauStop, px, py, pz);
-        return;
-      }
-      if (step >= P.max_steps) {
-        finish(kStepLimit, px, py, pz);
-        return;
-      }
+      if (P.tau_stop > 0.f && tau_hi + tau_lo >= P.tau_stop) stop = kTauStop;
+      else if (step >= P.max_steps) stop = kStepLimit;
     }
-    if (P.ckpt && (step % kCkptEvery) == 0) {
+    if (active && stop == 0 && P.ckpt && (step % kCkptEvery) == 0) {
       // state at node `step` for the adjoint's recomputation (bounded by the ray's allocation)
       const unsigned int item = C.item;
       const unsigned long long slot = P.ck_off[item] + (unsigned long long)(step / kCkptEvery);
@@ -266,6 +266,7 @@ __global__ void __launch_bounds__(kThreads, kRayMinBlocks) trace_rays(const __gr
     }
 
     // ---------------------------------------------- (c) complete step `step`
+    const float qx = px, qy = py, qz = pz;  // node `step` (a stopped path ends there)
     Vec dr, rn, kn;
     complete_step<kMixed>(h, P.h2_6, P.h_6, o, px, py, pz, kx, ky, kz, rlx, rly, rlz, klx, kly, klz, dr, rn, kn);
     kap_prev = kap;
@@ -277,14 +278,17 @@ __global__ void __launch_bounds__(kThreads, kRayMinBlocks) trace_rays(const __gr
     else if (!isfinite(rr2 + kn.x + kn.y + kn.z)) term = kNan;
 
     // ---------------------------------------------- (d) neighbour retrace of step `step`
-    if (NB > 0 && term != kNan) {
+    if (NB > 0) {
       const Retrace R = retrace_step<NB>(P.G, kf, h, P.h2_6, P.h2_12, P.eta, P.eps_fixed, px, py, pz, kx, ky, kz,
                                          dr, Vec{o.Gx, o.Gy, o.Gz});
-      acc_add<kMixed>(lns_hi, lns_lo, R.lm);
+      if (stop == 0 && term != kNan) acc_add<kMixed>(lns_hi, lns_lo, R.lm);
     }
+    if (!active) return;
 
     // ---------------------------------------------- (e) next node, or the end of the path
-    if (term == 0) {
+    if (stop != 0) {
+      finish(stop, qx, qy, qz);
+    } else if (term == 0) {
       px = rn.x; py = rn.y; pz = rn.z;
       kx = kn.x; ky = kn.y; kz = kn.z;
       step += 1;
@@ -353,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, kRayMinBlocks) trace_rays(const __gr
       needmask = __ballot_sync(kFull, need);
     }
     if (!__any_sync(kFull, active)) break;
-    if (active) step_once();
+    step_once();
   }
 
   // ---- statistics
