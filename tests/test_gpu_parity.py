@@ -229,6 +229,39 @@ def test_field_probe_matches_oracle(rt, ctx, orc):
     assert len(bad) <= 4, (len(bad), bad[:3])
 
 
+def test_field_probe_vacuum_boundary(rt, ctx, orc):
+    """Vacuum beyond r_vac = r_max (1 + 1e-6) (reading R4): inside the band the
+    last cell extends linearly, as in the oracle; beyond it n_e, T_e and the
+    gradient are exactly zero, out to radii far past the grid.  Radii stay
+    several FP32 ulps away from r_vac so both sides agree on the side."""
+    import torch
+    g = smooth_grid()
+    g32 = cs.Grid(g.r, g.theta, g.phi, g.ne.astype(np.float32).astype(np.float64),
+                  g.te.astype(np.float32).astype(np.float64))
+    grid = ctx.load(g)
+    F = orc.grid_field(g32)
+    rng = np.random.default_rng(11)
+    r_max = float(g.r[-1])
+    scales = np.array([1 - 1e-3, 1 - 1e-7, 1 + 2e-7, 1 + 3e-6, 1 + 1e-3, 1.5, 10.0, 1e3])
+    d = rng.normal(size=(400, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    pts = (d * (r_max * scales[np.arange(400) % len(scales)])[:, None]).astype(np.float32).astype(np.float64)
+    out = ctx.probe_field(grid, pts).cpu().numpy().astype(np.float64)
+    torch.cuda.synchronize()
+    r_vac = r_max * (1 + 1e-6)
+    for p, o in zip(pts, out):
+        r = np.linalg.norm(p)
+        ne, gr, te = orc.field_eval(F, p)
+        if r > r_vac:
+            assert ne == 0.0 and te == 0.0 and not gr.any(), (r, ne, te)
+            assert (o == 0.0).all(), (p, r, o)
+        else:
+            assert ne > 0 and te > 0
+            assert abs(o[0] - ne) <= 1e-5 * abs(ne), (p, o[0], ne)
+            assert abs(o[1] - te) <= 1e-5 * abs(te), (p, o[1], te)
+            assert np.linalg.norm(o[2:] - gr) <= 1e-3 * np.linalg.norm(gr) + 1e-6 * abs(ne), (p, o[2:], gr)
+
+
 # ------------------------------------------------------------ strict parity
 
 def test_tiny_full_map_mixed(rt, ctx, orc, tiny):
