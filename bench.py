@@ -629,9 +629,11 @@ def run_forms(ctx, grid, v, f, prec, stream):
 def run_adjoint(ctx):
     """Adjoint/forward time ratio on the differentiation workload (128x90x180
     corona, 256^2 x 8 frequencies 40-400 MHz) for the misfit
-    L = sum (T_b - T_target)^2 against the maps of its perturbed grid:
-    rt_backward given the forward's diagnostics (the autograd path) over the
-    forward, in both arithmetic forms."""
+    L = sum (T_b - T_target)^2 against the maps of its perturbed grid, in
+    both arithmetic forms: the autograd path (the forward keeps a tape,
+    rt_trace_image_tape; the backward reverses it, rt_backward_tape) over the
+    plain forward (rt_trace_image); also rt_backward given the forward's
+    diagnostics (it traces twice more) and standalone."""
     import torch
 
     import corona_synth as cs
@@ -641,7 +643,9 @@ def run_adjoint(ctx):
     grid_t = ctx.load(cs.perturbed_target(ga))
     adjoint = {"workload": "Newkirk 128x90x180 grid, 256x256 x 8 freq 40-400 MHz, 4 neighbours",
                "loss": "sum (T_b - T_target)^2, T_target traced through the perturbed grid",
-               "ratio_definition": "backward given the forward's per-ray diagnostics (the autograd path) / forward; "
+               "ratio_definition": "ratio: rt_backward_tape (the autograd backward) / rt_trace_image; "
+                                   "tape_forward_s: rt_trace_image_tape (the autograd forward); "
+                                   "ratio_retrace: rt_backward given the forward's diagnostics / rt_trace_image; "
                                    "ratio_standalone: rt_backward with its own counting pass"}
     for nm, pr in (("mixed", rt.RT_MIXED), ("plain", rt.RT_PLAIN_F32)):
         oa = rt.options(precision=pr)
@@ -664,7 +668,23 @@ def run_adjoint(ctx):
         ctx.backward(grid_a, va, fa, wgt, oa)
         torch.cuda.synchronize()
         tbs = time.perf_counter() - t0
-        adjoint[nm] = {"forward_s": tf, "backward_s": tbk, "ratio": tbk / tf,
+        ctx.trace_image_tape(grid_a, va, fa, oa)[2].free()  # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, tape = ctx.trace_image_tape(grid_a, va, fa, oa)
+        torch.cuda.synchronize()
+        tft = time.perf_counter() - t0
+        used, cap = tape.info()
+        tape.backward(wgt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tape.backward(wgt)
+        torch.cuda.synchronize()
+        tbt = time.perf_counter() - t0
+        tape.free()
+        adjoint[nm] = {"forward_s": tf, "tape_forward_s": tft, "backward_s": tbt, "ratio": tbt / tf,
+                       "tape_slots_used": used, "tape_slots_cap": cap,
+                       "backward_retrace_s": tbk, "ratio_retrace": tbk / tf,
                        "backward_standalone_s": tbs, "ratio_standalone": tbs / tf}
     grid_a.free()
     grid_t.free()

@@ -111,7 +111,7 @@ typedef struct {
   int straight;     /* 1: straight lines of sight, n = 1, no magnification           */
   int precision;    /* RT_PLAIN_F32 or RT_MIXED (compensated state and accumulators) */
   int tile;         /* launch: rt_trace_image takes pixels in tile x tile blocks (2..32); */
-                    /* 0 = row by row.  Results do not depend on it.                   */
+                    /* 0 = 64-pixel chunks, longest first.  Results do not depend on it. */
   int blocks_per_sm;/* launch: persistent blocks per SM; 0 = as many as fit              */
 } rt_options;
 
@@ -146,7 +146,9 @@ rt_status rt_destroy(rt_ctx* ctx);
 
 /* Copies the grid into library-owned device memory, converted to FP32 and
  * repacked cell by cell (the 8 corner values of each cell contiguous, for
- * n_e and T_e), and builds the radial lookup table.  Synchronous: returns
+ * n_e and T_e; 64 B per cell, plus one all-zero shell of cells that the
+ * lookup selects beyond r_max (1 + 1e-6), the vacuum), and builds the radial
+ * lookup table.  Synchronous: returns
  * after the copy and a device-side value check; the caller may free ne/te
  * afterwards.  Errors: RT_ERR_ARG (null pointers), RT_ERR_GRID (node
  * arrays not monotone / not uniform where required, non-finite or negative
@@ -156,14 +158,22 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* desc, const void* ne, co
 rt_status rt_free_grid(rt_ctx* ctx, rt_grid* grid);
 
 /* Traces one image at nf frequencies (Sec. 3.2-3.3): for every pixel and
- * frequency one ray bundle (the central ray and its n_nb neighbours on
- * adjacent lanes of a warp), stepped with RK4, with the tube magnification
- * and the free-free transfer accumulated along the way.
+ * frequency one ray bundle (the central ray and its n_nb neighbours: one
+ * thread per bundle in the step-wise forms and with magnification off,
+ * adjacent lanes of a warp in tube mode), stepped with RK4, with the tube
+ * magnification and the free-free transfer accumulated along the way.
  * freqs_hz: host, nf entries (1 <= nf <= 64), each > 0.
  * tb_out:   device, [nf][ny][nx] float, caller-owned, fully overwritten.
  * diag:     device, [nf][ny][nx] rt_ray_diag, or NULL.
+ * Work order: with opt->tile = 0 the rays are taken in 64-pixel chunks of
+ * all frequencies, longest estimated paths first (as a batch plan orders
+ * them), from a work table that the call stages in the context's pinned
+ * host buffer and copies into a stream-ordered device allocation freed
+ * after the launch; a call may wait for the previous call's table copy to
+ * leave that buffer.  opt->tile > 0: tiles of each frequency in turn,
+ * lowest frequency first, no table.  Results do not depend on the order.
  * Asynchronous on `stream`.  Errors: RT_ERR_ARG, RT_ERR_UNSUPPORTED,
- * RT_ERR_CUDA. */
+ * RT_ERR_OOM, RT_ERR_CUDA. */
 rt_status rt_trace_image(rt_ctx* ctx, const rt_grid* grid, const rt_view* view,
                          const double* freqs_hz, int nf, const rt_options* opt,
                          float* tb_out, rt_ray_diag* diag, void* stream);
@@ -242,18 +252,51 @@ rt_status rt_trace_batch(rt_ctx* ctx, const rt_grid* grid, const rt_request* req
  * tb_out:  device [nf][ny][nx] float for the forward T_b (0 for rays with a
  *          zero weight), or NULL.
  * fwd_diag: optional device [nf][ny][nx] rt_ray_diag that rt_trace_image
- *          returned for the same grid, view, frequencies and options (an
- *          autograd forward keeps it).  The checkpoints are sized from its
+ *          returned for the same grid, view, frequencies and options.  The
+ *          checkpoints are sized from its
  *          step counts and the first forward pass is skipped.  NULL: the
  *          call traces the rays once more to count their steps.  A diag
  *          whose step counts differ from this forward's gives RT_ERR_ARG
  *          (no ray reads another ray's checkpoints).
  * Synchronous: returns when the gradients are complete.  Allocates and
- * frees its own device scratch (checkpoints ~ total ray steps / 32 x 64 B).
+ * frees its own device scratch (checkpoints ~ total ray steps / 32 x 68 B).
  * Errors: RT_ERR_ARG, RT_ERR_UNSUPPORTED, RT_ERR_OOM, RT_ERR_CUDA. */
 rt_status rt_backward(rt_ctx* ctx, const rt_grid* grid, const rt_view* view, const double* freqs_hz, int nf,
                       const rt_options* opt, const float* dL_dTb, float* dL_dne, float* dL_dte, float* tb_out,
                       const rt_ray_diag* fwd_diag, void* stream);
+
+/* An adjoint tape: the forward of rt_trace_image, run once with the ray
+ * state stored every 32 central steps, so that rt_backward_tape reverses it
+ * without tracing the rays again (rt_backward traces them twice more).  The
+ * forward is the arithmetic of rt_trace_image: T_b and the diagnostics are
+ * identical (no tile walk: opt->tile is ignored).
+ * view, freqs_hz, nf, opt: as for rt_backward (its supported forms).
+ * pool_bytes: device memory for the stored states, 72 B per started
+ *          32-step segment of every ray; 0 sizes the pool at 1.5 times an
+ *          estimate from the entry chords cut at each frequency's turning
+ *          radius.  A pool that overflows leaves the tape usable:
+ *          rt_backward_tape then traces twice more, as rt_backward does.
+ * tb_out:  device [nf][ny][nx] float, caller-owned.
+ * diag:    device [nf][ny][nx] rt_ray_diag, caller-owned, kept by the tape
+ *          until rt_backward_tape; or NULL (the tape holds its own).
+ * out:     the tape; it refers to grid, which must outlive it.  Release it
+ *          with rt_tape_free.
+ * Asynchronous on stream.  Errors: RT_ERR_ARG, RT_ERR_UNSUPPORTED,
+ * RT_ERR_OOM, RT_ERR_CUDA. */
+typedef struct rt_tape rt_tape;
+rt_status rt_trace_image_tape(rt_ctx* ctx, const rt_grid* grid, const rt_view* view, const double* freqs_hz,
+                              int nf, const rt_options* opt, size_t pool_bytes, float* tb_out, rt_ray_diag* diag,
+                              rt_tape** out, void* stream);
+/* The gradient of sum dL_dTb * T_b (as rt_backward) from a tape: only the
+ * reverse sweep runs.  dL_dTb, dL_dne, dL_dte as for rt_backward.  A tape may
+ * be reversed more than once (for several weight maps).  Synchronous.
+ * Errors: RT_ERR_ARG (NULL argument, or checkpoints missing for a ray),
+ * RT_ERR_CUDA. */
+rt_status rt_backward_tape(rt_tape* tape, const float* dL_dTb, float* dL_dne, float* dL_dte, void* stream);
+/* Pool slots the tape's forward took and the pool's capacity (used > cap:
+ * it overflowed).  Waits for stream. */
+rt_status rt_tape_info(rt_tape* tape, void* stream, unsigned long long* slots_used, unsigned long long* slots_cap);
+rt_status rt_tape_free(rt_tape* tape);
 
 /* Allocation-free batch.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory when they trace:

@@ -18,7 +18,7 @@ from . import _abi
 from ._abi import (RT_MAG_OFF, RT_MIXED, RT_PLAIN_F32, RT_STEPWISE, RT_TUBE, RAY_STATUS, RtError,
                    check, lib)
 
-__all__ = ["Context", "Grid", "BatchPlan", "RayTraceFn", "options", "view", "RtError", "RT_STEPWISE", "RT_TUBE", "RT_MAG_OFF",
+__all__ = ["Context", "Grid", "BatchPlan", "Tape", "RayTraceFn", "options", "view", "RtError", "RT_STEPWISE", "RT_TUBE", "RT_MAG_OFF",
            "RT_PLAIN_F32", "RT_MIXED", "RAY_STATUS", "diag_to_numpy"]
 
 
@@ -59,6 +59,48 @@ class Grid:
     def free(self):
         if self.handle and self.ctx.handle:
             check(lib().rt_free_grid(self.ctx.handle, self.handle), "rt_free_grid")
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Tape:
+    """An adjoint tape (rt_tape): the forward of trace_image_tape with its
+    checkpoints, reversed by backward() without tracing the rays again."""
+
+    def __init__(self, ctx: "Context", handle: C.c_void_p, grid: Grid, nf: int, ny: int, nx: int, diag):
+        self.ctx = ctx
+        self.handle = handle
+        self.grid = grid      # the tape refers to the grid: keep it alive
+        self.shape = (nf, ny, nx)
+        self.diag = diag      # the caller-visible diagnostics the tape keeps
+
+    def backward(self, dL_dTb, stream=None):
+        """rt_backward_tape: (dL/dn_e, dL/dT_e) of sum(dL_dTb * T_b), float32
+        CUDA tensors shaped like the grid."""
+        import torch
+        dev = torch.device("cuda", self.ctx.device)
+        g = torch.as_tensor(dL_dTb, dtype=torch.float32, device=dev).contiguous()
+        assert g.numel() == self.shape[0] * self.shape[1] * self.shape[2]
+        dne = torch.empty(self.grid.shape, dtype=torch.float32, device=dev)
+        dte = torch.empty(self.grid.shape, dtype=torch.float32, device=dev)
+        check(lib().rt_backward_tape(self.handle, C.c_void_p(g.data_ptr()), C.c_void_p(dne.data_ptr()),
+                                     C.c_void_p(dte.data_ptr()), _stream_ptr(stream)), "rt_backward_tape")
+        return dne, dte
+
+    def info(self, stream=None):
+        """(pool slots taken, pool capacity); taken > capacity: it overflowed."""
+        used, cap = C.c_ulonglong(0), C.c_ulonglong(0)
+        check(lib().rt_tape_info(self.handle, _stream_ptr(stream), C.byref(used), C.byref(cap)), "rt_tape_info")
+        return int(used.value), int(cap.value)
+
+    def free(self):
+        if self.handle:
+            check(lib().rt_tape_free(self.handle), "rt_tape_free")
         self.handle = None
 
     def __del__(self):
@@ -207,6 +249,27 @@ class Context:
                                    _stream_ptr(stream)), "rt_trace_image")
         return (out, d) if diag else out
 
+    def trace_image_tape(self, grid: Grid, v, freqs, opts=None, pool_bytes=0, stream=None):
+        """rt_trace_image_tape: T_b [nf, ny, nx] (as trace_image), the
+        diagnostics [nf, ny, nx, 7] and a Tape whose backward() gives the
+        gradients without tracing again.  pool_bytes = 0: sized from an
+        estimate of the path lengths."""
+        import torch
+        vs = view(v)
+        f = np.ascontiguousarray(np.atleast_1d(freqs), dtype=np.float64)
+        nf = len(f)
+        dev = torch.device("cuda", self.device)
+        out = torch.empty((nf, vs.ny, vs.nx), dtype=torch.float32, device=dev)
+        d = torch.empty((nf, vs.ny, vs.nx, 7), dtype=torch.int32, device=dev)
+        o = opts if opts is not None else options()
+        h = C.c_void_p()
+        check(lib().rt_trace_image_tape(self.handle, grid.handle, C.byref(vs),
+                                        f.ctypes.data_as(C.POINTER(C.c_double)), nf, C.byref(o),
+                                        C.c_size_t(int(pool_bytes)), C.c_void_p(out.data_ptr()),
+                                        C.c_void_p(d.data_ptr()), C.byref(h), _stream_ptr(stream)),
+              "rt_trace_image_tape")
+        return out, d, Tape(self, h, grid, nf, vs.ny, vs.nx, d)
+
     def batch_plan(self, grid: Grid, requests, opts=None, diag=False) -> BatchPlan:
         """rt_batch_plan_create over requests (objects with .view and .freqs_hz)."""
         return BatchPlan(self, grid, requests, opts, diag)
@@ -327,7 +390,8 @@ def diag_to_numpy(d):
 
 class RayTraceFn:
     """torch.autograd.Function: T_b maps from grid tensors, differentiable
-    with respect to n_e and T_e through rt_backward.
+    with respect to n_e and T_e: the forward keeps an adjoint tape
+    (rt_trace_image_tape), the backward reverses it (rt_backward_tape).
 
         tb = RayTraceFn.apply(ne, te, ctx, r, theta, phi, view, freqs, opts)
 
@@ -341,14 +405,24 @@ class RayTraceFn:
             @staticmethod
             def forward(fctx, ne, te, ctx, r, theta, phi, v, freqs, opts):
                 grid = ctx.load_grid(r, theta, phi, ne.detach(), te.detach())
-                tb, d = ctx.trace_image(grid, v, freqs, opts, diag=True)
-                fctx.state = (ctx, grid, v, freqs, opts, ne.dtype, te.dtype, d)
+                o = opts if opts is not None else options()
+                differentiable = (not o.straight) and (o.s_mode == RT_MAG_OFF or (o.s_mode == RT_STEPWISE
+                                                                                  and o.n_nb == 4))
+                if differentiable and any(fctx.needs_input_grad[:2]):
+                    tb, _, tape = ctx.trace_image_tape(grid, v, freqs, o)
+                else:  # no gradient wanted, or a form the adjoint does not cover
+                    tb, tape = ctx.trace_image(grid, v, freqs, o), None
+                fctx.state = (grid, tape, ne.dtype, te.dtype)
                 return tb
 
             @staticmethod
             def backward(fctx, grad_tb):
-                ctx, grid, v, freqs, opts, dne_t, dte_t, d = fctx.state
-                dne, dte = ctx.backward(grid, v, freqs, grad_tb.contiguous(), opts, fwd_diag=d)
+                grid, tape, dne_t, dte_t = fctx.state
+                if tape is None:
+                    raise RuntimeError("RayTraceFn: the adjoint covers step-wise magnification with 4 "
+                                       "neighbours or magnification off, not straight lines or tube mode")
+                dne, dte = tape.backward(grad_tb.contiguous())
+                tape.free()
                 grid.free()
                 return dne.to(dne_t), dte.to(dte_t), None, None, None, None, None, None, None
 

@@ -25,7 +25,8 @@ EXPORTS = ["rt_default_options", "rt_status_string", "rt_last_error", "rt_create
            "rt_load_grid", "rt_free_grid", "rt_trace_image", "rt_backward", "rt_batch_plan_create",
            "rt_batch_plan_create_shard", "rt_shard_assign", "rt_batch_plan_launch",
            "rt_batch_plan_stats", "rt_batch_plan_destroy", "rt_trace_batch", "rt_trace_batch_noalloc",
-           "rt_probe_field", "rt_disk_mean_tb", "rt_beam_convolve", "rt_trace_paths", "rt_sync", "rt_get_stats"]
+           "rt_probe_field", "rt_disk_mean_tb", "rt_beam_convolve", "rt_trace_paths", "rt_sync", "rt_get_stats",
+           "rt_trace_image_tape", "rt_backward_tape", "rt_tape_info", "rt_tape_free"]
 
 
 class GridDesc(C.Structure):
@@ -111,11 +112,17 @@ def lib():
                                      ip, vp, vp, vp, vp, vp]
         L.rt_sync.argtypes = [vp, vp]
         L.rt_get_stats.argtypes = [vp, vp, C.POINTER(Stats)]
+        L.rt_trace_image_tape.argtypes = [vp, vp, C.POINTER(View), C.POINTER(C.c_double), ip, C.POINTER(Options),
+                                          C.c_size_t, vp, vp, C.POINTER(vp), vp]
+        L.rt_backward_tape.argtypes = [vp, vp, vp, vp, vp]
+        L.rt_tape_info.argtypes = [vp, vp, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)]
+        L.rt_tape_free.argtypes = [vp]
         for name in ("rt_create", "rt_destroy", "rt_load_grid", "rt_free_grid", "rt_trace_image", "rt_backward",
                      "rt_batch_plan_create", "rt_batch_plan_create_shard", "rt_shard_assign",
                      "rt_batch_plan_launch", "rt_batch_plan_stats",
                      "rt_batch_plan_destroy", "rt_trace_batch", "rt_trace_batch_noalloc", "rt_probe_field",
-                     "rt_disk_mean_tb", "rt_beam_convolve", "rt_trace_paths", "rt_sync", "rt_get_stats"):
+                     "rt_disk_mean_tb", "rt_beam_convolve", "rt_trace_paths", "rt_sync", "rt_get_stats",
+                     "rt_trace_image_tape", "rt_backward_tape", "rt_tape_info", "rt_tape_free"):
             getattr(L, name).restype = ip
         _lib = L
         return _lib

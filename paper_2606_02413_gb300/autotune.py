@@ -8,7 +8,8 @@ For a (grid, view, frequencies) workload it chooses
   computed by this library.  The step is part of the method's result (the
   step-wise magnification is first order in it), so the gate, not speed,
   decides it;
-* the launch shape: the pixel walk (row by row or tiles of 4, 8, 16) and
+* the launch shape: the pixel walk (64-pixel chunks longest first, or each
+  frequency in tiles of 4, 8, 16) and
   the persistent blocks per SM, timed with CUDA events on a reduced image
   of the workload at the chosen step (results do not depend on them).
 

@@ -61,7 +61,7 @@ __device__ __forceinline__ CellGeom cell_geom(const GridDev& G, float x, float y
   c.inv_r = inv_r;
   c.rho = rho;
   c.inv_rho = inv_rho;
-  const float tt = (atan2_grid(rho, z) - G.t0) * G.t_inv;
+  const float tt = (atan2_grid<true>(rho, z) - G.t0) * G.t_inv;
   if (tt > 0.f && tt < G.t_last) {
     c.j = min(__float2int_rd(tt), G.n_t - 2);
     c.v = tt - (float)c.j;
@@ -127,14 +127,50 @@ __device__ __forceinline__ Vec value_adjoint(const GridDev& G, float x, float y,
           an * c.du.z + bn * c.dv.z + cn * c.dw.z};
 }
 
+// Per-thread accumulator of the n_e node adjoints of one cell, in shared
+// memory laid out [corner][thread] (a warp's accesses hit distinct banks).
+// The force adjoints of a step lie within a few 1e-3 R_sun of its node, and
+// mostly in the node's cell: they add here, and the sums reach the grid with
+// 8 atomics when the node moves to another cell or the ray ends, instead of
+// 8 atomics per force adjoint.  Stage points in another cell scatter directly.
+struct NodeAcc {
+  float* v;    // v[q * kThreads], corner q = 4 a + 2 b + c
+  int* key;    // the cell held (-1: none)
+  long* base;  // node index of its corner (0, 0, 0)
+  int* dk1;    // k1 - k: 1, or 1 - n_phi across the phi seam
+};
+
+__device__ __forceinline__ void acc_flush(const GridDev& G, const NodeAcc& A, float* dne) {
+  if (*A.key < 0) return;
+  const long b0 = *A.base, sr = (long)G.n_t * G.n_p;
+  const int dk = *A.dk1;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float x = A.v[q * kThreads];
+    if (x != 0.f) atomicAdd(dne + b0 + (q >> 2) * sr + ((q >> 1) & 1) * G.n_p + (q & 1) * dk, x);
+    A.v[q * kThreads] = 0.f;
+  }
+  *A.key = -1;
+}
+
 // Force adjoint at one RK4 stage: the force is a = kf grad n_e(p).  Given
-// lam = dL/da, scatters kf lam . grad w_c to the n_e nodes and returns
-// kf H(p) lam (the position adjoint), H from dual numbers with the cell fixed.
+// lam = dL/da, scatters kf lam . grad w_c to the n_e nodes (through the
+// accumulator A when p lies in its cell; adopt: p is a node, whose cell the
+// accumulator takes over) and returns kf H(p) lam (the position adjoint), H
+// from dual numbers with the cell fixed.
 __device__ __forceinline__ Vec force_adjoint(const GridDev& G, float kf, float x, float y, float z, const Vec& lam,
-                                             float* dne) {
+                                             float* dne, const NodeAcc& acc, bool adopt) {
   if (lam.x == 0.f && lam.y == 0.f && lam.z == 0.f) return {0.f, 0.f, 0.f};
   const CellGeom c = cell_geom(G, x, y, z);
   if (c.vac) return {0.f, 0.f, 0.f};
+  const int cell = (c.i * (G.n_t - 1) + c.j) * G.n_p + c.k;
+  if (adopt && cell != *acc.key) {
+    acc_flush(G, acc, dne);
+    *acc.key = cell;
+    *acc.base = node_index(G, c, 0, 0, 0);
+    *acc.dk1 = c.k1 - c.k;
+  }
+  const bool hit = cell == *acc.key;
   // node scatter
   const float gu = lam.x * c.du.x + lam.y * c.du.y + lam.z * c.du.z;
   const float gv = lam.x * c.dv.x + lam.y * c.dv.y + lam.z * c.dv.z;
@@ -148,7 +184,8 @@ __device__ __forceinline__ Vec force_adjoint(const GridDev& G, float kf, float x
 #pragma unroll
       for (int cc = 0; cc < 2; ++cc) {
         const float coef = sg[a] * wv[b] * ww[cc] * gu + wu[a] * sg[b] * ww[cc] * gv + wu[a] * wv[b] * sg[cc] * gw;
-        atomicAdd(dne + node_index(G, c, a, b, cc), kf * coef);
+        if (hit) acc.v[(a * 4 + b * 2 + cc) * kThreads] += kf * coef;
+        else atomicAdd(dne + node_index(G, c, a, b, cc), kf * coef);
       }
   // Hessian-vector product: tangent of grad n_e along lam.  The tangents of
   // the fractions are lam . grad (u, v, w) = (gu, gv, gw); those of r, rho
@@ -160,7 +197,6 @@ __device__ __forceinline__ Vec force_adjoint(const GridDev& G, float kf, float x
   const Dl rho{c.rho, rho_d};
   const Dl inv_rho{c.inv_rho, -rho_d * c.inv_rho * c.inv_rho};
   const float2 rc = __ldg(G.r_cell + c.i);
-  const int cell = (c.i * (G.n_t - 1) + c.j) * G.n_p + c.k;
   const float4 c0 = __ldg(G.ne + 2 * cell), c1 = __ldg(G.ne + 2 * cell + 1);
   const float d00 = c0.y - c0.x, d01 = c0.w - c0.z, d10 = c1.y - c1.x, d11 = c1.w - c1.z;
   const Dl W{c.w, gw};
@@ -200,7 +236,7 @@ __device__ __forceinline__ Vec force_adjoint(const GridDev& G, float kf, float x
 // (the kernel's instruction footprint, not its arithmetic, bounds it).
 __device__ __forceinline__ void rk4_reverse_any(const GridDev& G, float kf, float h, const Vec& p, const Vec& k,
                                                 const Vec& lr, const Vec& lk, const Vec& lg, int nst, Vec& lp,
-                                                Vec& lko, float* dne) {
+                                                Vec& lko, float* dne, const NodeAcc& A) {
   const float hh = 0.5f * h, h6 = h / 6.f, h3 = h / 3.f;
   // forward stage points (kept in registers: the stage loop selects among them)
   const Vec P2{fmaf(hh, k.x, p.x), fmaf(hh, k.y, p.y), fmaf(hh, k.z, p.z)};
@@ -228,7 +264,8 @@ __device__ __forceinline__ void rk4_reverse_any(const GridDev& G, float kf, floa
   for (int s = nst - 1; s >= 0; --s) {
     const Vec pt = (s == 3) ? P4 : (s == 2) ? P3 : (s == 1) ? P2 : p;
     const Vec la = (s == 3) ? La4 : (s == 2) ? La3 : (s == 1) ? La2 : La1;
-    const Vec LP = force_adjoint(G, kf, pt.x, pt.y, pt.z, la, dne);
+    // the central ray's stage 1 is the node: the accumulator follows it
+    const Vec LP = force_adjoint(G, kf, pt.x, pt.y, pt.z, la, dne, A, nst == 4 && s == 0);
     Lp = {Lp.x + LP.x, Lp.y + LP.y, Lp.z + LP.z};
     if (s == 3) {         // P4 = p + h k3, k3 = k + h/2 a2
       Lk3 = {fmaf(h, LP.x, Lk3.x), fmaf(h, LP.y, Lk3.y), fmaf(h, LP.z, Lk3.z)};
@@ -271,7 +308,9 @@ struct AdjParams {
   const RayDiag* diag;         // forward diagnostics (steps, status), output order
   const float* dL_dTb;         // [nf][npix], output order
   const Ckpt* ckpt;
-  const unsigned long long* ck_off;
+  const unsigned long long* ck_off;  // ray t owns ckpt[ck_off[t] .. ck_off[t+1]); or, a tape:
+  const int* ck_prev;                // the pool's links to each ray's previous checkpoint
+  const int* ck_last;                // and each ray's last checkpoint
   float* dne;
   float* dte;
   unsigned int* counter;
@@ -308,11 +347,19 @@ __global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_rays(const __
   const int lane = threadIdx.x & 31;
   const float h = P.h;
   StepRec R[K + 1];
+  __shared__ float acc_v[8 * kThreads];
+  __shared__ int acc_key[kThreads], acc_dk1[kThreads];
+  __shared__ long acc_base[kThreads];
+  const NodeAcc A{acc_v + threadIdx.x, acc_key + threadIdx.x, acc_base + threadIdx.x, acc_dk1 + threadIdx.x};
+#pragma unroll
+  for (int q = 0; q < 8; ++q) A.v[q * kThreads] = 0.f;
+  *A.key = -1;
 
   // per-ray state of the reverse sweep
   unsigned int item = 0;
   bool active = false, exhausted = false;
   int N = 0, status = 0, seg = 0;
+  int slot = -1;  // tape: the pool slot of segment seg's checkpoint
   bool clipped = false;
   float kf = 0.f, kn2 = 0.f, kap_c = 0.f, ln_f = 0.f, lamT = 0.f, alpha = 1.f;
   float Wsuf = 0.f;                   // weight of everything beyond the node (sum of later terms)
@@ -343,8 +390,10 @@ __global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_rays(const __
           // the checkpoints were sized from a step count: it must be this ray's
           const unsigned long long n_ck =
               (d.steps > 0 && lw != 0.f) ? (unsigned long long)((d.steps - 1) / K + 1) : 0ull;
-          const bool fits = P.ck_off[item + 1] - P.ck_off[item] == n_ck;
+          // a tape's chain is checked segment by segment (the checkpoint's step)
+          const bool fits = P.ck_prev ? true : P.ck_off[item + 1] - P.ck_off[item] == n_ck;
           if (!fits) atomicAdd(P.mismatch, 1ull);
+          if (P.ck_prev) slot = P.ck_last[item];
           if (fits && d.steps > 0 && d.status >= kExitOuter && d.status <= kStepLimit && lw != 0.f) {
             N = d.steps;
             status = d.status;
@@ -372,8 +421,15 @@ __global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_rays(const __
     const int n_s = min(K, N - m0);
     const bool last_seg = (m0 + n_s == N);
     float px, py, pz, kx, ky, kz, rlx, rly, rlz, klx, kly, klz, tau, lns;
+    if (P.ck_prev && (slot < 0 || P.ckpt[slot].step != m0)) {
+      // the tape does not hold this segment: the diagnostics belong to another forward
+      atomicAdd(P.mismatch, 1ull);
+      acc_flush(P.G, A, P.dne);
+      active = false;
+      continue;
+    }
     {
-      const Ckpt& c = P.ckpt[P.ck_off[item] + seg];
+      const Ckpt& c = P.ckpt[P.ck_prev ? (unsigned long long)slot : P.ck_off[item] + seg];
       px = c.r[0]; py = c.r[1]; pz = c.r[2];
       kx = c.k[0]; ky = c.k[1]; kz = c.k[2];
       rlx = c.rl[0]; rly = c.rl[1]; rlz = c.rl[2];
@@ -573,7 +629,7 @@ __global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_rays(const __
           lp_o = {lp_o.x - ldr.x, lp_o.y - ldr.y, lp_o.z - ldr.z};
           lk_in = Lk;
         }
-        rk4_reverse_any(P.G, kf, h, base, rk, lr_in, lk_in, lg, (q < NB) ? 3 : 4, lp_o, lk_o, P.dne);
+        rk4_reverse_any(P.G, kf, h, base, rk, lr_in, lk_in, lg, (q < NB) ? 3 : 4, lp_o, lk_o, P.dne, A);
         if (q < NB) {
           slp = {slp.x + lp_o.x, slp.y + lp_o.y, slp.z + lp_o.z};
           slk = {slk.x + lk_o.x, slk.y + lk_o.y, slk.z + lk_o.z};
@@ -588,8 +644,13 @@ __global__ void __launch_bounds__(kThreads, kAdjMinBlocks) adjoint_rays(const __
     }
 
     // ------------------------------------------------ next segment / done
-    if (seg == 0) active = false;
-    else seg -= 1;
+    if (seg == 0) {
+      acc_flush(P.G, A, P.dne);
+      active = false;
+    } else {
+      seg -= 1;
+      if (P.ck_prev) slot = P.ck_prev[slot];
+    }
   }
 }
 

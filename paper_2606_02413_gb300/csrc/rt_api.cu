@@ -58,6 +58,13 @@ struct rt_ctx {
   int sm_count = 0;
   unsigned int* d_counter = nullptr;        // work-queue ticket
   unsigned long long* d_stats = nullptr;    // [2]
+  // pinned staging of rt_trace_image's work tables; stage_done follows the
+  // last copy out of it (the next call waits for it before refilling)
+  std::mutex stage_mu;
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaEvent_t stage_done = nullptr;
+  bool stage_pending = false;
 };
 
 struct rt_grid {
@@ -82,6 +89,26 @@ struct rt_batch_plan {
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+};
+
+// A forward with its checkpoints kept for the reverse sweep.
+struct rt_tape {
+  rt_ctx* ctx = nullptr;
+  const rt_grid* g = nullptr;
+  rt_view view{};
+  std::vector<double> freqs;
+  rt_options opt{};
+  int nb = 0;
+  bool mixed = true;
+  TraceParams P{};                  // the forward's parameters (frequency order, view)
+  Ckpt* pool = nullptr;
+  int* prev = nullptr;
+  int* last = nullptr;
+  unsigned long long* counter = nullptr;  // [0] pool slots taken, [1] the adjoint's mismatch count
+  unsigned long long cap = 0;
+  RayDiag* diag = nullptr;
+  bool own_diag = false;
+  long total = 0;
 };
 
 // --------------------------------------------------------------- kernels
@@ -362,6 +389,11 @@ rt_status rt_create(rt_ctx** out, int device) {
 rt_status rt_destroy(rt_ctx* ctx) {
   if (!ctx) return fail(RT_ERR_ARG, "rt_destroy: ctx is NULL");
   cudaSetDevice(ctx->device);
+  if (ctx->stage_done) {
+    cudaEventSynchronize(ctx->stage_done);
+    cudaEventDestroy(ctx->stage_done);
+  }
+  cudaFreeHost(ctx->stage);
   cudaFree(ctx->d_counter);
   cudaFree(ctx->d_stats);
   delete ctx;
@@ -664,6 +696,45 @@ double turning_radius(const rt_grid* g, double f) {
   return 0.0;
 }
 
+struct ChunkCand {
+  double cost;  // estimated steps of the chunk's rays (every 8th pixel sampled)
+  ChunkDev c;
+};
+
+// The maps (one per frequency) and 64-pixel chunks of one image request, as
+// view q of a work table; chunk costs from path_estimate.
+void request_chunks(const rt_grid* g, const rt_view& V, const double* freqs, int nf, int q, float* tb_out,
+                    rt_ray_diag* diag, std::vector<MapDev>& maps, std::vector<ChunkCand>& cands) {
+  const double rmin = g->r.front(), rmax = g->r.back();
+  const int npix = V.nx * V.ny;
+  const double du = (V.x1 - V.x0) / V.nx, dv = (V.y1 - V.y0) / V.ny;
+  for (int fi = 0; fi < nf; ++fi) {
+    MapDev M;
+    M.f = make_freq(freqs[fi], fi);
+    M.view = q;
+    M.out = tb_out + (size_t)fi * npix;
+    M.diag = diag ? reinterpret_cast<RayDiag*>(diag) + (size_t)fi * npix : nullptr;
+    const int m = (int)maps.size();
+    maps.push_back(M);
+    const double rc = turning_radius(g, freqs[fi]);
+    for (int p0 = 0; p0 < npix; p0 += kChunk) {
+      const int cnt = std::min(kChunk, npix - p0);
+      double cost = 0.0;
+      for (int k = 0; k < cnt; k += 8) {
+        const int pix = p0 + k, ix = pix % V.nx, iy = pix / V.nx;
+        const double u = V.x0 + (ix + 0.5) * du, v = V.y0 + (iy + 0.5) * dv;
+        cost += path_estimate(std::sqrt(u * u + v * v), rc, rmin, rmax);
+      }
+      cands.push_back({cost, ChunkDev{m, p0, cnt, 0}});
+    }
+  }
+}
+
+void sort_longest_first(std::vector<ChunkCand>& cands) {
+  std::stable_sort(cands.begin(), cands.end(), [](const ChunkCand& a, const ChunkCand& b) { return a.cost > b.cost; });
+}
+
+
 }  // namespace
 
 extern "C" {
@@ -702,9 +773,59 @@ rt_status rt_trace_image(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const 
 
   RT_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  RT_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), s));
-  RT_CUDA(cudaMemsetAsync(ctx->d_stats, 0, 2 * sizeof(unsigned long long), s));
-  RT_CUDA(dispatch_trace(nb, o->precision == RT_MIXED, P, ctx->sm_count, s, is_tube(o)));
+  void* d_tables = nullptr;
+  if (o->tile <= 0) {
+    // row order: the 64-pixel chunks of all frequencies, longest first (the
+    // batch plans' order; a ray's arithmetic does not depend on it), through
+    // a work table uploaded from the context's pinned staging
+    std::vector<MapDev> maps;
+    std::vector<ChunkCand> cands;
+    request_chunks(g, *v, freqs, nf, 0, tb_out, diag, maps, cands);
+    sort_longest_first(cands);
+    const size_t off_maps = (sizeof(ViewDev) + 15) / 16 * 16;
+    const size_t off_chunks = off_maps + (sizeof(MapDev) * maps.size() + 15) / 16 * 16;
+    const size_t bytes = off_chunks + sizeof(ChunkDev) * cands.size();
+    std::lock_guard<std::mutex> lock(ctx->stage_mu);
+    cudaError_t e = cudaSuccess;
+    if (ctx->stage_pending) e = cudaEventSynchronize(ctx->stage_done);  // the previous copy has left the buffer
+    ctx->stage_pending = false;
+    if (e == cudaSuccess && ctx->stage_bytes < bytes) {
+      cudaFreeHost(ctx->stage);
+      ctx->stage = nullptr;
+      ctx->stage_bytes = 0;
+      e = cudaMallocHost(&ctx->stage, bytes);
+      if (e == cudaSuccess) ctx->stage_bytes = bytes;
+    }
+    if (e == cudaSuccess && !ctx->stage_done) e = cudaEventCreateWithFlags(&ctx->stage_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return fail(RT_ERR_CUDA, "rt_trace_image: %s", cudaGetErrorString(e));
+    char* h = static_cast<char*>(ctx->stage);
+    const ViewDev vd = make_view(*v);
+    std::memcpy(h, &vd, sizeof vd);
+    std::memcpy(h + off_maps, maps.data(), sizeof(MapDev) * maps.size());
+    for (size_t i = 0; i < cands.size(); ++i) std::memcpy(h + off_chunks + i * sizeof(ChunkDev), &cands[i].c, sizeof(ChunkDev));
+    e = cudaMallocAsync(&d_tables, bytes, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tables, h, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->stage_done, s);
+    if (e != cudaSuccess) {
+      if (d_tables) cudaFreeAsync(d_tables, s);
+      return fail(e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "rt_trace_image: %s",
+                  cudaGetErrorString(e));
+    }
+    ctx->stage_pending = true;
+    char* d = static_cast<char*>(d_tables);
+    P.views = reinterpret_cast<const ViewDev*>(d);
+    P.maps = reinterpret_cast<const MapDev*>(d + off_maps);
+    P.chunks = reinterpret_cast<const ChunkDev*>(d + off_chunks);
+    P.total = (unsigned int)(cands.size() * kChunk);
+  }
+  cudaError_t e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_stats, 0, 2 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = dispatch_trace(nb, o->precision == RT_MIXED, P, ctx->sm_count, s, is_tube(o));
+  if (d_tables) {
+    const cudaError_t e2 = cudaFreeAsync(d_tables, s);  // stream-ordered: after the kernel
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e != cudaSuccess) return fail(RT_ERR_CUDA, "rt_trace_image: %s", cudaGetErrorString(e));
   return RT_OK;
 }
 
@@ -755,41 +876,19 @@ static rt_status plan_create(rt_ctx* ctx, const rt_grid* g, const rt_request* re
   if (st != RT_OK) return st;
   std::vector<ViewDev> views;
   std::vector<MapDev> maps;
-  struct Cand { double cost; ChunkDev c; };
-  std::vector<Cand> cands;
-  const double rmin = g->r.front(), rmax = g->r.back();
+  std::vector<ChunkCand> cands;
   for (int q = 0; q < nreq; ++q) {
     const rt_request& R = reqs[q];
     if (!R.view || !R.freqs_hz || !R.tb_out || R.nf < 1) return fail(RT_ERR_ARG, "request %d: NULL field or nf < 1", q);
     st = check_view(R.view);
     if (st != RT_OK) return st;
-    views.push_back(make_view(*R.view));
-    const int npix = R.view->nx * R.view->ny;
-    const double du = (R.view->x1 - R.view->x0) / R.view->nx, dv = (R.view->y1 - R.view->y0) / R.view->ny;
-    for (int fi = 0; fi < R.nf; ++fi) {
+    for (int fi = 0; fi < R.nf; ++fi)
       if (bad_freq(R.freqs_hz[fi])) return fail(RT_ERR_ARG, "request %d frequency %d is not > 0", q, fi);
-      MapDev M;
-      M.f = make_freq(R.freqs_hz[fi], fi);
-      M.view = q;
-      M.out = R.tb_out + (size_t)fi * npix;
-      M.diag = R.diag ? reinterpret_cast<RayDiag*>(R.diag) + (size_t)fi * npix : nullptr;
-      const int m = (int)maps.size();
-      maps.push_back(M);
-      const double rc = turning_radius(g, R.freqs_hz[fi]);
-      for (int p0 = 0; p0 < npix; p0 += kChunk) {
-        const int cnt = std::min(kChunk, npix - p0);
-        double cost = 0.0;
-        for (int k = 0; k < cnt; k += 8) {
-          const int pix = p0 + k, ix = pix % R.view->nx, iy = pix / R.view->nx;
-          const double u = R.view->x0 + (ix + 0.5) * du, v = R.view->y0 + (iy + 0.5) * dv;
-          cost += path_estimate(std::sqrt(u * u + v * v), rc, rmin, rmax);
-        }
-        cands.push_back({cost, ChunkDev{m, p0, cnt, 0}});
-      }
-    }
+    views.push_back(make_view(*R.view));
+    request_chunks(g, *R.view, R.freqs_hz, R.nf, q, R.tb_out, R.diag, maps, cands);
   }
   if ((double)cands.size() * kChunk >= 4.0e9) return fail(RT_ERR_ARG, "rt_batch_plan_create: too many rays");
-  std::stable_sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) { return a.cost > b.cost; });
+  sort_longest_first(cands);
   std::vector<ChunkDev> chunks;
   if (world_size == 1) {
     chunks.resize(cands.size());
@@ -886,23 +985,102 @@ rt_status rt_trace_batch(rt_ctx* ctx, const rt_grid* g, const rt_request* reqs, 
   return RT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Checks shared by the adjoint's entry points; nb_out: the neighbour count.
+rt_status check_backward(const rt_view* v, const double* freqs, int nf, const rt_options* o, int* nb_out,
+                         const char* who) {
+  rt_status st = check_view(v);
+  if (st != RT_OK) return st;
+  st = check_options(o, nb_out);
+  if (st != RT_OK) return st;
+  if (o->straight || o->s_mode == RT_TUBE || !(*nb_out == 0 || *nb_out == 4))
+    return fail(RT_ERR_UNSUPPORTED, "%s: supports step-wise magnification with 4 neighbours or none", who);
+  if (nf < 1 || nf > kMaxFreq) return fail(RT_ERR_ARG, "%s: nf = %d (1..%d)", who, nf, kMaxFreq);
+  for (int i = 0; i < nf; ++i)
+    if (bad_freq(freqs[i])) return fail(RT_ERR_ARG, "frequency %d is not > 0", i);
+  if ((long)nf * v->nx * v->ny >= (1L << 31)) return fail(RT_ERR_ARG, "%s: too many rays", who);
+  return RT_OK;
+}
+
+// The forward parameters of the adjoint's passes: image mode without a tile
+// walk (ticket t = frequency in ascending order, then pixel).
+void backward_params(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const double* freqs, int nf,
+                     const rt_options* o, float* tb, RayDiag* diag, TraceParams& P, std::vector<int>& order) {
+  std::memset(&P, 0, sizeof P);
+  fill_common(P, g, o);
+  P.view = make_view(*v);
+  P.nf = nf;
+  order.resize(nf);
+  for (int i = 0; i < nf; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return freqs[a] < freqs[b]; });
+  for (int i = 0; i < nf; ++i) P.freq[i] = make_freq(freqs[order[i]], order[i]);
+  P.tb_out = tb;
+  P.diag = diag;
+  P.counter = ctx->d_counter;
+  P.stats = ctx->d_stats;
+  P.total = (unsigned int)((long)nf * v->nx * v->ny);
+}
+
+// Zeroes the gradients and launches the reverse sweep over the checkpoints
+// (ck_off, or a tape's ck_prev / ck_last chains).
+cudaError_t launch_adjoint(rt_ctx* ctx, const rt_grid* g, const TraceParams& P, int nb, bool mixed,
+                           const RayDiag* diag, const float* dL_dTb, float* dL_dne, float* dL_dte, const Ckpt* ckpt,
+                           const unsigned long long* ck_off, const int* ck_prev, const int* ck_last,
+                           unsigned long long* mismatch, cudaStream_t s) {
+  const size_t nodes = (size_t)g->n_r * g->n_t * g->n_p;
+  cudaError_t e = cudaMemsetAsync(dL_dne, 0, sizeof(float) * nodes, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dL_dte, 0, sizeof(float) * nodes, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(mismatch, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  AdjParams A;
+  std::memset(&A, 0, sizeof A);
+  A.G = g->dev;
+  A.h = P.h; A.h2_6 = P.h2_6; A.h_6 = P.h_6; A.h2_12 = P.h2_12; A.hrsun = P.hrsun;
+  A.eta = P.eta; A.eps_fixed = P.eps_fixed; A.tbc_K = P.tbc_K; A.tbc_mode = P.tbc_mode; A.emission = P.emission;
+  A.view = P.view;
+  A.nf = P.nf;
+  for (int i = 0; i < P.nf; ++i) A.freq[i] = P.freq[i];
+  A.diag = diag;
+  A.dL_dTb = dL_dTb;
+  A.ckpt = ckpt;
+  A.ck_off = ck_off;
+  A.ck_prev = ck_prev;
+  A.ck_last = ck_last;
+  A.dne = dL_dne;
+  A.dte = dL_dte;
+  A.counter = ctx->d_counter;
+  A.total = P.total;
+  A.mismatch = mismatch;
+  const int per_sm = (nb == 0) ? (mixed ? adj_blocks_per_sm<0, true>() : adj_blocks_per_sm<0, false>())
+                               : (mixed ? adj_blocks_per_sm<4, true>() : adj_blocks_per_sm<4, false>());
+  const int grid_blocks = ctx->sm_count * per_sm;
+  if (nb == 0) {
+    if (mixed) adjoint_rays<0, true><<<grid_blocks, kThreads, 0, s>>>(A);
+    else adjoint_rays<0, false><<<grid_blocks, kThreads, 0, s>>>(A);
+  } else {
+    if (mixed) adjoint_rays<4, true><<<grid_blocks, kThreads, 0, s>>>(A);
+    else adjoint_rays<4, false><<<grid_blocks, kThreads, 0, s>>>(A);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
 rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const double* freqs, int nf, const rt_options* o,
                       const float* dL_dTb, float* dL_dne, float* dL_dte, float* tb_out, const rt_ray_diag* fwd_diag,
                       void* stream) {
   if (!ctx || !g || !freqs || !dL_dTb || !dL_dne || !dL_dte) return fail(RT_ERR_ARG, "rt_backward: NULL argument");
-  rt_status st = check_view(v);
-  if (st != RT_OK) return st;
   int nb = 0;
-  st = check_options(o, &nb);
+  rt_status st = check_backward(v, freqs, nf, o, &nb, "rt_backward");
   if (st != RT_OK) return st;
-  if (o->straight || o->s_mode == RT_TUBE || !(nb == 0 || nb == 4))
-    return fail(RT_ERR_UNSUPPORTED, "rt_backward: supports step-wise magnification with 4 neighbours or none");
-  if (nf < 1 || nf > kMaxFreq) return fail(RT_ERR_ARG, "rt_backward: nf = %d (1..%d)", nf, kMaxFreq);
-  for (int i = 0; i < nf; ++i)
-    if (bad_freq(freqs[i])) return fail(RT_ERR_ARG, "frequency %d is not > 0", i);
   const long npix = (long)v->nx * v->ny;
   const long total = (long)nf * npix;
-  if (total >= (1L << 31)) return fail(RT_ERR_ARG, "rt_backward: too many rays");
   const bool mixed = o->precision == RT_MIXED;
   RT_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
@@ -930,19 +1108,8 @@ rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const dou
 
   // phase 0: forward with per-ray step counts
   TraceParams P;
-  std::memset(&P, 0, sizeof P);
-  fill_common(P, g, o);
-  P.view = make_view(*v);
-  P.nf = nf;
-  std::vector<int> order(nf);
-  for (int i = 0; i < nf; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return freqs[a] < freqs[b]; });
-  for (int i = 0; i < nf; ++i) P.freq[i] = make_freq(freqs[order[i]], order[i]);
-  P.tb_out = tb;
-  P.diag = diag;
-  P.counter = ctx->d_counter;
-  P.stats = ctx->d_stats;
-  P.total = (unsigned int)total;
+  std::vector<int> order;
+  backward_params(ctx, g, v, freqs, nf, o, tb, diag, P, order);
   P.skip_zero = dL_dTb;
   auto run_forward = [&]() -> cudaError_t {
     cudaError_t r = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), s);
@@ -981,48 +1148,17 @@ rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const dou
         (d.steps > 0 && hw[o] != 0.f) ? (unsigned long long)((d.steps - 1) / kCkptEvery + 1) : 0ull;
     off[t + 1] = off[t] + cnt;
   }
-  const int per_sm = (nb == 0) ? (mixed ? adj_blocks_per_sm<0, true>() : adj_blocks_per_sm<0, false>())
-                               : (mixed ? adj_blocks_per_sm<4, true>() : adj_blocks_per_sm<4, false>());
-  const int grid_blocks = ctx->sm_count * per_sm;
   e = cudaMalloc(&ckpt, sizeof(Ckpt) * std::max<unsigned long long>(off[total], 1ull));
   if (e == cudaSuccess) e = cudaMemcpyAsync(ck_off, off.data(), sizeof(unsigned long long) * (total + 1),
                                             cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ck_off + total + 1, 0, sizeof(unsigned long long), s);
   // phase 1: the same forward again, storing checkpoints
   P.ckpt = ckpt;
   P.ck_off = ck_off;
   if (e == cudaSuccess) e = run_forward();
   // phase 2: reverse sweep
-  if (e == cudaSuccess) e = cudaMemsetAsync(dL_dne, 0, sizeof(float) * (size_t)g->n_r * g->n_t * g->n_p, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(dL_dte, 0, sizeof(float) * (size_t)g->n_r * g->n_t * g->n_p, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), s);
-  if (e == cudaSuccess) {
-    AdjParams A;
-    std::memset(&A, 0, sizeof A);
-    A.G = g->dev;
-    A.h = P.h; A.h2_6 = P.h2_6; A.h_6 = P.h_6; A.h2_12 = P.h2_12; A.hrsun = P.hrsun;
-    A.eta = P.eta; A.eps_fixed = P.eps_fixed; A.tbc_K = P.tbc_K; A.tbc_mode = P.tbc_mode; A.emission = P.emission;
-    A.view = P.view;
-    A.nf = nf;
-    for (int i = 0; i < nf; ++i) A.freq[i] = P.freq[i];
-    A.diag = diag;
-    A.dL_dTb = dL_dTb;
-    A.ckpt = ckpt;
-    A.ck_off = ck_off;
-    A.dne = dL_dne;
-    A.dte = dL_dte;
-    A.counter = ctx->d_counter;
-    A.total = (unsigned int)total;
-    A.mismatch = ck_off + total + 1;
-    if (nb == 0) {
-      if (mixed) adjoint_rays<0, true><<<grid_blocks, kThreads, 0, s>>>(A);
-      else adjoint_rays<0, false><<<grid_blocks, kThreads, 0, s>>>(A);
-    } else {
-      if (mixed) adjoint_rays<4, true><<<grid_blocks, kThreads, 0, s>>>(A);
-      else adjoint_rays<4, false><<<grid_blocks, kThreads, 0, s>>>(A);
-    }
-    e = cudaGetLastError();
-  }
+  if (e == cudaSuccess)
+    e = launch_adjoint(ctx, g, P, nb, mixed, diag, dL_dTb, dL_dne, dL_dte, ckpt, ck_off, nullptr, nullptr,
+                       ck_off + total + 1, s);
   unsigned long long mismatch = 0;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&mismatch, ck_off + total + 1, sizeof mismatch, cudaMemcpyDeviceToHost, s);
@@ -1033,6 +1169,123 @@ rt_status rt_backward(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const dou
   if (mismatch)
     return fail(RT_ERR_ARG, "rt_backward: fwd_diag does not match this forward (%llu rays with other step counts)",
                 mismatch);
+  return RT_OK;
+}
+
+rt_status rt_tape_free(rt_tape* t) {
+  if (!t) return fail(RT_ERR_ARG, "rt_tape_free: NULL tape");
+  if (t->ctx) cudaSetDevice(t->ctx->device);
+  cudaFree(t->pool);
+  cudaFree(t->prev);
+  cudaFree(t->last);
+  cudaFree(t->counter);
+  if (t->own_diag) cudaFree(t->diag);
+  delete t;
+  return RT_OK;
+}
+
+rt_status rt_trace_image_tape(rt_ctx* ctx, const rt_grid* g, const rt_view* v, const double* freqs, int nf,
+                              const rt_options* o, size_t pool_bytes, float* tb_out, rt_ray_diag* diag, rt_tape** out,
+                              void* stream) {
+  if (!ctx || !g || !freqs || !tb_out || !out) return fail(RT_ERR_ARG, "rt_trace_image_tape: NULL argument");
+  *out = nullptr;
+  int nb = 0;
+  rt_status st = check_backward(v, freqs, nf, o, &nb, "rt_trace_image_tape");
+  if (st != RT_OK) return st;
+  const long npix = (long)v->nx * v->ny;
+  const long total = (long)nf * npix;
+  // pool: the given bytes, or 1.5 x the estimated checkpoints (the entry chord
+  // cut at the turning radius, in steps of h, one checkpoint per kCkptEvery)
+  unsigned long long cap = pool_bytes / (sizeof(Ckpt) + sizeof(int));
+  if (pool_bytes == 0) {
+    const double rmin = g->r.front(), rmax = g->r.back(), h = o->dtau;
+    const double du = (v->x1 - v->x0) / v->nx, dv = (v->y1 - v->y0) / v->ny;
+    double est = 0.0;
+    for (int fi = 0; fi < nf; ++fi) {
+      const double rc = turning_radius(g, freqs[fi]);
+      for (int iy = 0; iy < v->ny; ++iy)
+        for (int ix = 0; ix < v->nx; ++ix) {
+          const double u = v->x0 + (ix + 0.5) * du, w = v->y0 + (iy + 0.5) * dv;
+          est += path_estimate(std::sqrt(u * u + w * w), rc, rmin, rmax) / h / kCkptEvery + 1.0;
+        }
+    }
+    cap = (unsigned long long)(1.5 * est) + 1024;
+  }
+  cap = std::min<unsigned long long>(std::max<unsigned long long>(cap, 1), (unsigned long long)std::numeric_limits<int>::max());
+  RT_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  rt_tape* t = new rt_tape;
+  t->ctx = ctx;
+  t->g = g;
+  t->view = *v;
+  t->freqs.assign(freqs, freqs + nf);
+  t->opt = *o;
+  t->nb = nb;
+  t->mixed = o->precision == RT_MIXED;
+  t->cap = cap;
+  t->total = total;
+  cudaError_t e = cudaMalloc(&t->pool, sizeof(Ckpt) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&t->prev, sizeof(int) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&t->last, sizeof(int) * total);
+  if (e == cudaSuccess) e = cudaMalloc(&t->counter, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess && !diag) {
+    e = cudaMalloc(&t->diag, sizeof(RayDiag) * total);
+    t->own_diag = true;
+  } else if (diag) {
+    t->diag = reinterpret_cast<RayDiag*>(diag);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->last, 0xff, sizeof(int) * total, s);  // -1: no checkpoint
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->counter, 0, 2 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) {
+    rt_tape_free(t);
+    return fail(e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, "rt_trace_image_tape: %s",
+                cudaGetErrorString(e));
+  }
+  std::vector<int> order;
+  backward_params(ctx, g, v, freqs, nf, o, tb_out, t->diag, t->P, order);
+  t->P.ckpt = t->pool;
+  t->P.ck_prev = t->prev;
+  t->P.ck_last = t->last;
+  t->P.pool_counter = t->counter;
+  t->P.pool_cap = cap;
+  e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_stats, 0, 2 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = dispatch_trace(nb, t->mixed, t->P, ctx->sm_count, s);
+  if (e != cudaSuccess) {
+    rt_tape_free(t);
+    return fail(RT_ERR_CUDA, "rt_trace_image_tape: %s", cudaGetErrorString(e));
+  }
+  *out = t;
+  return RT_OK;
+}
+
+rt_status rt_tape_info(rt_tape* t, void* stream, unsigned long long* slots_used, unsigned long long* slots_cap) {
+  if (!t || !slots_used || !slots_cap) return fail(RT_ERR_ARG, "rt_tape_info: NULL argument");
+  RT_CUDA(cudaSetDevice(t->ctx->device));
+  unsigned long long used = 0;
+  RT_CUDA(cudaMemcpyAsync(&used, t->counter, sizeof used, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  RT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  *slots_used = used;
+  *slots_cap = t->cap;
+  return RT_OK;
+}
+
+rt_status rt_backward_tape(rt_tape* t, const float* dL_dTb, float* dL_dne, float* dL_dte, void* stream) {
+  if (!t || !dL_dTb || !dL_dne || !dL_dte) return fail(RT_ERR_ARG, "rt_backward_tape: NULL argument");
+  unsigned long long used = 0, cap = 0;
+  rt_status st = rt_tape_info(t, stream, &used, &cap);
+  if (st != RT_OK) return st;
+  if (used > cap)  // the pool overflowed: trace again, as rt_backward does
+    return rt_backward(t->ctx, t->g, &t->view, t->freqs.data(), (int)t->freqs.size(), &t->opt, dL_dTb, dL_dne,
+                       dL_dte, nullptr, reinterpret_cast<const rt_ray_diag*>(t->diag), stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_adjoint(t->ctx, t->g, t->P, t->nb, t->mixed, t->diag, dL_dTb, dL_dne, dL_dte, t->pool,
+                                 nullptr, t->prev, t->last, t->counter + 1, s);
+  unsigned long long mismatch = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&mismatch, t->counter + 1, sizeof mismatch, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(RT_ERR_CUDA, "rt_backward_tape: %s", cudaGetErrorString(e));
+  if (mismatch) return fail(RT_ERR_ARG, "rt_backward_tape: %llu rays without their checkpoints", mismatch);
   return RT_OK;
 }
 

@@ -67,11 +67,14 @@ struct Sample {
 // atan2 for the grid lookup: the argument is reduced to a = min/max in [0, 1],
 // atan(a) = a P(a^2) with the degree-7 polynomial fitted by csrc/fit_atan.py
 // (max error 3.7e-8 in exact arithmetic, ~2e-7 rad after FP32 rounding), and
-// the quadrant of (x, y) restored.
+// the quadrant of (x, y) restored.  At x = y = 0 the floor on the divisor
+// gives a = 0 without a branch.  kYNonNeg: the caller guarantees y >= 0
+// (theta from rho >= 0), so the sign of y needs no restoring.
+template <bool kYNonNeg = false>
 __device__ __forceinline__ float atan2_grid(float y, float x) {
   const float ax = fabsf(x), ay = fabsf(y);
   const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-  const float a = (mx > 0.f) ? __fdividef(mn, mx) : 0.f;
+  const float a = __fdividef(mn, fmaxf(mx, 1e-30f));
   const float t = a * a;
   float p = -4.054565173e-03f;
   p = fmaf(p, t, 2.186295542e-02f);
@@ -84,7 +87,7 @@ __device__ __forceinline__ float atan2_grid(float y, float x) {
   float r = a * p;
   if (ay > ax) r = 1.57079632679489662f - r;
   if (x < 0.f) r = 3.14159265358979324f - r;
-  return copysignf(r, y);
+  return kYNonNeg ? r : copysignf(r, y);
 }
 
 // Trilinear interpolant in (r, theta, phi) (linear in physical r) and its
@@ -178,20 +181,16 @@ __device__ __forceinline__ Sample eval_field_t(const GridDev& G, float x, float 
   const int i = radial_lookup(G, r, R, inv_dr);
   const float u = (r - R) * inv_dr;
 
-  const float inv_rho = (rho2 > 0.f) ? rsqrtf(rho2) : 0.f;
+  // on the polar axis (rho = 0) the floor keeps inv_rho finite: rho = 0 and
+  // the theta and phi terms of the gradient vanish with x = y = 0
+  const float inv_rho = rsqrtf(fmaxf(rho2, 1e-20f));
   const float rho = rho2 * inv_rho;
-  const float tt = (atan2_grid(rho, z) - G.t0) * G.t_inv;
-  int j;
-  float v, tsel;
-  if (tt > 0.f && tt < G.t_last) {
-    j = min(__float2int_rd(tt), G.n_t - 2);
-    v = tt - (float)j;
-    tsel = 1.f;
-  } else if (tt <= 0.f) {
-    j = 0; v = 0.f; tsel = 0.f;
-  } else {
-    j = G.n_t - 2; v = 1.f; tsel = 0.f;
-  }
+  // theta cell: clamped to the outermost cells, where the fraction sticks
+  // at 0 or 1 and the theta derivative is off (tsel = 0)
+  const float tt = (atan2_grid<true>(rho, z) - G.t0) * G.t_inv;
+  const int j = min(max(__float2int_rd(tt), 0), G.n_t - 2);
+  const float v = fminf(fmaxf(tt - (float)j, 0.f), 1.f);
+  const float tsel = (tt > 0.f && tt < G.t_last) ? 1.f : 0.f;
   float ph = atan2_grid(y, x) - G.p0;
   if (ph < 0.f) ph += kTwoPiF;
   if (ph >= kTwoPiF) ph -= kTwoPiF;
@@ -250,7 +249,7 @@ __device__ __forceinline__ BasePoint base_point(const GridDev& G, float x, float
   const float r2 = fmaf(z, z, rho2);
   c.r = r2 * rsqrtf(r2);
   c.rho = rho2 * ((rho2 > 0.f) ? rsqrtf(rho2) : 0.f);
-  c.tt = (atan2_grid(c.rho, z) - G.t0) * G.t_inv;
+  c.tt = (atan2_grid<true>(c.rho, z) - G.t0) * G.t_inv;
   float ph = atan2_grid(y, x) - G.p0;
   if (ph < 0.f) ph += kTwoPiF;
   if (ph >= kTwoPiF) ph -= kTwoPiF;
@@ -529,9 +528,12 @@ struct ChunkDev {
 #define RT_CKPT_EVERY 32
 #endif
 constexpr int kCkptEvery = RT_CKPT_EVERY;
+// The state of a ray at node `step` (a multiple of kCkptEvery): what the
+// adjoint's recomputation of the following segment starts from.
 struct Ckpt {
   float r[3], k[3], rl[3], kl[3];
   float tau_hi, tau_lo, lns_hi, lns_lo;
+  int step;
 };
 
 struct TraceParams {
@@ -559,9 +561,16 @@ struct TraceParams {
   unsigned int* counter;            // work queue ticket (zeroed before launch)
   unsigned long long* stats;        // [0] ray steps, [1] rays
   unsigned int total;               // tickets
-  // optional checkpoints (image mode): ray t owns ckpt[ck_off[t] .. ck_off[t+1])
+  // optional checkpoints (image mode): ray t owns ckpt[ck_off[t] .. ck_off[t+1]);
+  // or, when ck_prev is set (a tape), each checkpoint takes the next pool slot
+  // (pool_counter, at most pool_cap), ck_prev links it to the ray's previous
+  // one (-1: none) and ck_last[t] names ray t's last one (-1: none)
   Ckpt* ckpt;
   const unsigned long long* ck_off;
+  int* ck_prev;
+  int* ck_last;
+  unsigned long long* pool_counter;
+  unsigned long long pool_cap;
   // optional (image mode): rays whose weight here is exactly 0 are not traced
   // (T_b 0, diagnostics zero); the adjoint's passes skip rays that cannot
   // contribute to the gradient

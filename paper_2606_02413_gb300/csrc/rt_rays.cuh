@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(kThreads, kRayMinBlocks) trace_rays(const __gr
     RayDiag* dg;
     unsigned long long steps_done, rays_done;
     unsigned int item;
+    int ck_last;  // tape: the ray's last checkpoint slot (-1: none)
   };
   __shared__ Cold cold[kThreads];
   Cold& C = cold[threadIdx.x];
@@ -203,6 +204,7 @@ __global__ void __launch_bounds__(kThreads, kRayMinBlocks) trace_rays(const __gr
   C.steps_done = 0;
   C.rays_done = 0;
   C.item = 0;
+  C.ck_last = -1;
   int step = 0;
   bool active = false, exhausted = false;
   float px = 0.f, py = 0.f, pz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
@@ -223,6 +225,7 @@ __global__ void __launch_bounds__(kThreads, kRayMinBlocks) trace_rays(const __gr
       d.status = st;
       *dg = d;
     }
+    if (P.ck_last) P.ck_last[C.item] = C.ck_last;
     C.steps_done += (unsigned long long)step;
     C.rays_done += 1;
     active = false;
@@ -251,10 +254,19 @@ __global__ void __launch_bounds__(kThreads, kRayMinBlocks) trace_rays(const __gr
       else if (step >= P.max_steps) stop = kStepLimit;
     }
     if (active && stop == 0 && P.ckpt && (step % kCkptEvery) == 0) {
-      // state at node `step` for the adjoint's recomputation (bounded by the ray's allocation)
-      const unsigned int item = C.item;
-      const unsigned long long slot = P.ck_off[item] + (unsigned long long)(step / kCkptEvery);
-      if (slot < P.ck_off[item + 1]) {
+      // state at node `step` for the adjoint's recomputation: in the ray's
+      // own slots, or (a tape) in the next pool slot, linked to its previous
+      unsigned long long slot;
+      bool ok;
+      if (P.ck_prev) {
+        slot = atomicAdd(P.pool_counter, 1ull);
+        ok = slot < P.pool_cap;  // an overflowing tape is detected from the counter
+      } else {
+        const unsigned int item = C.item;
+        slot = P.ck_off[item] + (unsigned long long)(step / kCkptEvery);
+        ok = slot < P.ck_off[item + 1];
+      }
+      if (ok) {
         Ckpt& c = P.ckpt[slot];
         c.r[0] = px; c.r[1] = py; c.r[2] = pz;
         c.k[0] = kx; c.k[1] = ky; c.k[2] = kz;
@@ -262,6 +274,11 @@ __global__ void __launch_bounds__(kThreads, kRayMinBlocks) trace_rays(const __gr
         c.kl[0] = klx; c.kl[1] = kly; c.kl[2] = klz;
         c.tau_hi = tau_hi; c.tau_lo = tau_lo;
         c.lns_hi = lns_hi; c.lns_lo = lns_lo;
+        c.step = step;
+        if (P.ck_prev) {
+          P.ck_prev[slot] = C.ck_last;
+          C.ck_last = (int)slot;
+        }
       }
     }
 
@@ -335,6 +352,7 @@ __global__ void __launch_bounds__(kThreads, kRayMinBlocks) trace_rays(const __gr
           C.item = item;
           C.out = rs.out;
           C.dg = rs.dg;
+          C.ck_last = -1;
           if (rs.valid) {  // a ragged chunk tail has no ray behind the ticket: take another
             kf = P.straight ? 0.f : rs.F->kf;
             kap_c = rs.F->kap_c;

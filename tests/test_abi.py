@@ -88,6 +88,10 @@ def test_null_arguments_fail_cleanly(L):
     assert L.rt_destroy(None) == _abi.RT_ERR_ARG
     assert L.rt_sync(None, None) == _abi.RT_ERR_ARG
     assert L.rt_get_stats(None, None, None) == _abi.RT_ERR_ARG
+    assert L.rt_trace_image_tape(None, None, None, None, 1, None, 0, None, None, None, None) == _abi.RT_ERR_ARG
+    assert L.rt_backward_tape(None, None, None, None, None) == _abi.RT_ERR_ARG
+    assert L.rt_tape_info(None, None, None, None) == _abi.RT_ERR_ARG
+    assert L.rt_tape_free(None) == _abi.RT_ERR_ARG
 
 
 def test_no_gpu_is_an_error_not_a_fallback(L):

@@ -131,6 +131,44 @@ def test_backward_reuses_forward_diag(rt, ctx):
         ctx.backward(grid, v, [60e6], w, opts, fwd_diag=d_other)
 
 
+def test_tape_forward_and_reverse(rt, ctx):
+    """rt_trace_image_tape: the forward of rt_trace_image (identical T_b and
+    diagnostics) with one pool slot per started 32-step segment of every ray;
+    rt_backward_tape gives rt_backward's gradients, is linear in the weights
+    and can be reversed again; a pool that overflows falls back to tracing
+    again, with the same gradients."""
+    import torch
+    g = smooth_grid()
+    v = cs.View(0.3, 0.1, 6, 5, -1.8, 1.8, -1.6, 1.6)
+    f = [60e6, 250e6]
+    grid = ctx.load(g)
+    opts = rt.options(precision=1, dtau=1e-2)
+    tb_t, d_t, tape = ctx.trace_image_tape(grid, v, f, opts)
+    tb, d = ctx.trace_image(grid, v, f, opts, diag=True)
+    torch.cuda.synchronize()
+    assert torch.equal(tb_t, tb) and torch.equal(d_t, d)
+    steps = d[..., 5].cpu().numpy().astype(np.int64)
+    used, cap = tape.info()
+    assert used == int(((steps - 1) // 32 + 1)[steps > 0].sum()) and used <= cap
+    w = torch.as_tensor(np.random.default_rng(5).normal(size=(len(f), v.ny, v.nx)), dtype=torch.float32,
+                        device="cuda")
+    a = tape.backward(w)
+    a2 = tape.backward(2 * w)
+    b = ctx.backward(grid, v, f, w, opts)
+    small = ctx.trace_image_tape(grid, v, f, opts, pool_bytes=72 * 3)[2]
+    su, sc = small.info()
+    assert sc == 3 and su > sc
+    c = small.backward(w)
+    torch.cuda.synchronize()
+    for x, x2, y, z in zip(a, a2, b, c):  # equal up to the order of the float atomics
+        tol = 1e-30 + 1e-5 * y.abs().max().item()
+        assert torch.allclose(x, y, rtol=1e-4, atol=tol)
+        assert torch.allclose(2 * x, x2, rtol=1e-4, atol=2 * tol)
+        assert torch.allclose(z, y, rtol=1e-4, atol=tol)
+    tape.free()
+    small.free()
+
+
 @pytest.fixture(scope="module")
 def misfit_case(orc):
     """The differentiation workload (128x90x180 corona, 256x256 x 8 frequencies
