@@ -319,9 +319,12 @@ struct AdjParams {
 };
 
 #ifndef RT_ADJ_MIN_BLOCKS
-#define RT_ADJ_MIN_BLOCKS 4
+#define RT_ADJ_MIN_BLOCKS 3
 #endif
-constexpr int kAdjMinBlocks = RT_ADJ_MIN_BLOCKS;  // occupancy target (128-thread blocks)
+// occupancy target (128-thread blocks): at 3 the kernel keeps its registers
+// without spills and its resident step records take a quarter less of
+// L1 and L2 than at 4
+constexpr int kAdjMinBlocks = RT_ADJ_MIN_BLOCKS;
 
 // One recomputed step of a segment (node m = m0 + j), in the thread's local
 // memory (the reverse reads it back last to first).
