@@ -428,13 +428,14 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
     if (std::fabs(Ph[k] - (Ph[0] + k * dph)) > 1e-9)
       return fail(RT_ERR_GRID, "rt_load_grid: phi nodes must be uniform with n_phi * dphi = 2 pi");
 
-  // radial lookup: bins no wider than the narrowest cell hold at most one node
+  // radial lookup: bins no wider than the narrowest cell hold at most one node;
+  // they start at r = 0, so the bin index of any radius is non-negative
   std::vector<float> Rf(nr);
   for (int i = 0; i < nr; ++i) Rf[i] = (float)R[i];
   double wmin = 1e300;
   for (int i = 0; i + 1 < nr; ++i) wmin = std::min(wmin, (double)Rf[i + 1] - (double)Rf[i]);
   if (!(wmin > 0)) return fail(RT_ERR_GRID, "rt_load_grid: r nodes collapse in FP32");
-  const double span = (double)Rf[nr - 1] - (double)Rf[0];
+  const double span = (double)Rf[nr - 1];
   const double nb_d = std::ceil(span / wmin) + 1.0;
   if (nb_d > (double)(1 << 22)) return fail(RT_ERR_GRID, "rt_load_grid: radial spacing too uneven for the lookup table");
   const int nb = (int)nb_d;
@@ -447,7 +448,7 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
   const float r_vac_split = std::nextafter(r_vac_f, std::numeric_limits<float>::infinity());
   std::vector<RadBin> lut(nb);
   for (int b = 0; b < nb; ++b) {
-    const double lo = (double)Rf[0] + b * bw, hi = lo + bw;
+    const double lo = b * bw, hi = lo + bw;
     int base = (int)(std::upper_bound(Rf.begin(), Rf.end(), (float)lo) - Rf.begin()) - 1;
     base = std::min(std::max(base, 0), nr - 2);
     while (base > 0 && (double)Rf[base] > lo) --base;
@@ -560,7 +561,6 @@ rt_status rt_load_grid(rt_ctx* ctx, const rt_grid_desc* d, const void* ne, const
   G.r_cell = g->rcell;
   G.n_r = nr; G.n_t = nt; G.n_p = np;
   G.r_lut_n = nb;
-  G.r_lut0 = Rf[0];
   G.r_lut_inv = (float)(nb / span);
   G.r_min = Rf[0];
   G.r_max = Rf[nr - 1];

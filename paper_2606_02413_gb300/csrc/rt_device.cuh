@@ -45,7 +45,7 @@ struct GridDev {
   const float2* r_cell;  // [n_r - 1]: (R_i, 1 / (R_{i+1} - R_i))
   int n_r, n_t, n_p;
   int r_lut_n;
-  float r_lut0, r_lut_inv;
+  float r_lut_inv;             // radial bins from r = 0, each 1 / r_lut_inv wide
   float r_min, r_max, r_vac;  // r_vac = r_max (1 + 1e-6): beyond it, vacuum
   float t0, t_inv, t_last;    // theta_0, 1 / dtheta, n_t - 1
   float p0, p_inv;            // phi_0, n_p / (2 pi)
@@ -153,8 +153,8 @@ __device__ __forceinline__ Sample vacuum_sample() {
 
 // Radial cell of r and its base radius and inverse width, from one bin.
 __device__ __forceinline__ int radial_lookup(const GridDev& G, float r, float& R, float& inv) {
-  int bin = __float2int_rd((r - G.r_lut0) * G.r_lut_inv);
-  bin = min(max(bin, 0), G.r_lut_n - 1);
+  // r >= 0 (and a NaN r converts to 0): only the top needs a clamp
+  const int bin = min(__float2int_rd(r * G.r_lut_inv), G.r_lut_n - 1);
   float base, split, r0, inv0, inv1, q0, q1, q2;
   ldg8(G.r_bins + bin, base, split, r0, inv0, inv1, q0, q1, q2);
   const bool up = r >= split;
