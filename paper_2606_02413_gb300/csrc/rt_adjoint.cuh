@@ -61,16 +61,12 @@ __device__ __forceinline__ CellGeom cell_geom(const GridDev& G, float x, float y
   c.inv_r = inv_r;
   c.rho = rho;
   c.inv_rho = inv_rho;
+  // theta cell as in the field evaluation: clamped to the outermost cells,
+  // where the fraction sticks at 0 or 1 and the theta derivative is off
   const float tt = (atan2_grid<true>(rho, z) - G.t0) * G.t_inv;
-  if (tt > 0.f && tt < G.t_last) {
-    c.j = min(__float2int_rd(tt), G.n_t - 2);
-    c.v = tt - (float)c.j;
-    c.tsel = 1.f;
-  } else if (tt <= 0.f) {
-    c.j = 0; c.v = 0.f; c.tsel = 0.f;
-  } else {
-    c.j = G.n_t - 2; c.v = 1.f; c.tsel = 0.f;
-  }
+  c.j = min(max(__float2int_rd(tt), 0), G.n_t - 2);
+  c.v = fminf(fmaxf(tt - (float)c.j, 0.f), 1.f);
+  c.tsel = (tt > 0.f && tt < G.t_last) ? 1.f : 0.f;
   float ph = atan2_grid(y, x) - G.p0;
   if (ph < 0.f) ph += kTwoPiF;
   if (ph >= kTwoPiF) ph -= kTwoPiF;
@@ -184,8 +180,11 @@ __device__ __forceinline__ Vec force_adjoint(const GridDev& G, float kf, float x
 #pragma unroll
       for (int cc = 0; cc < 2; ++cc) {
         const float coef = sg[a] * wv[b] * ww[cc] * gu + wu[a] * sg[b] * ww[cc] * gv + wu[a] * wv[b] * sg[cc] * gw;
-        if (hit) acc.v[(a * 4 + b * 2 + cc) * kThreads] += kf * coef;
-        else atomicAdd(dne + node_index(G, c, a, b, cc), kf * coef);
+        // both branches as straight-line code: the shared add takes 0 on a
+        // miss, the atomic is predicated (no divergence in the corner loop)
+        const float val = kf * coef;
+        acc.v[(a * 4 + b * 2 + cc) * kThreads] += hit ? val : 0.f;
+        if (!hit) atomicAdd(dne + node_index(G, c, a, b, cc), val);
       }
   // Hessian-vector product: tangent of grad n_e along lam.  The tangents of
   // the fractions are lam . grad (u, v, w) = (gu, gv, gw); those of r, rho
