@@ -61,6 +61,27 @@ def test_batch_equals_per_request_trace(rt, ctx, precision):
     plan.destroy()
 
 
+def test_image_work_orders_agree(rt, ctx):
+    """rt_trace_image's longest-first chunk order (tile = 0, through the
+    staged work table) and its tile walk give the same maps and diagnostics
+    bit for bit, on ragged images; the staging buffer grows for a larger
+    call and is reused by smaller ones."""
+    import torch
+    g, _, _ = cs.tiny_workload()
+    grid = ctx.load(g)
+    for nx, ny, nf in ((13, 7, 2), (96, 80, 3), (21, 34, 5)):
+        v = cs.View(0.4, -0.1, nx, ny, -2.4, 2.4, -2.1, 2.1)
+        f = list(cs.log_freqs(nf, 40e6, 800e6))
+        for precision in (0, 1):
+            a, da = ctx.trace_image(grid, v, f, rt.options(precision=precision), diag=True)
+            sa = ctx.stats()
+            b, db = ctx.trace_image(grid, v, f, rt.options(precision=precision, tile=8), diag=True)
+            sb = ctx.stats()
+            torch.cuda.synchronize()
+            assert torch.equal(a, b) and torch.equal(da, db)
+            assert sa == sb and sa["rays"] == nx * ny * nf
+
+
 def test_batch_matches_oracle_samples(rt, ctx, orc):
     import torch
     g, _, _ = cs.tiny_workload()
